@@ -1,0 +1,174 @@
+"""Statistical and structural properties of the oracle's index.
+
+* the LSH S-curve 1 - (1 - s^r)^b on planted pairs of exact Jaccard s
+  (the curve behind Eqs. 1-2);
+* the Bloom false-positive closed form (1 - e^{-kn/m})^k (Sec. 2.4);
+* no false negatives against an exact band-bucket index (the MinHashLSH
+  hash map of Sec. 2.3) replayed on the oracle's own insert decisions;
+* the stream decision of Sec. 2.1 on small hand-checked streams.
+"""
+import math
+
+import numpy as np
+import pytest
+
+
+def _binom_ok(hits, n, p, z=3.3):
+    sd = math.sqrt(max(p * (1 - p), 1e-12) / n)
+    return abs(hits / n - p) <= z * sd + 1.0 / n
+
+
+def _csr(docs):
+    lens = np.array([len(d) for d in docs], np.uint64)
+    off = np.zeros(len(docs) + 1, np.uint64)
+    np.cumsum(lens, out=off[1:])
+    toks = np.concatenate([np.asarray(d, np.uint32) for d in docs]) if docs else \
+        np.zeros(0, np.uint32)
+    return off, toks
+
+
+@pytest.mark.parametrize("s", [0.5, 0.7, 0.8, 0.9])
+def test_s_curve_on_planted_pairs(oracle, s):
+    """Pairs (A, B) of unigram sets with Jaccard exactly s, each pair on its own
+    token range.  B is flagged when some band collides with A; the flag rate
+    must match 1 - (1 - s^r)^b within a 99.9% binomial interval."""
+    b, r = 11, 11
+    rnd = np.random.default_rng(int(s * 100))
+    N = 100
+    # |A n B| = c, |A u B| = 2N - c, J = c / (2N - c)  ->  c = 2 N s / (1 + s)
+    c = int(round(2 * N * s / (1 + s)))
+    J = c / (2 * N - c)
+    pairs = 1500
+    docs = []
+    for t in range(pairs):
+        base = (t * 1000 + rnd.permutation(2 * N - c)).astype(np.uint32) + 1
+        docs.append(base[:N])
+        docs.append(np.concatenate([base[:c], base[N:]]))
+    off, toks = _csr(docs)
+    ix = oracle.OracleIndex(121, b, r, n_expected=10 * len(docs), fp_rate=1e-9, ngram=1,
+                            seed=3)
+    flags = ix.dedup(off, toks)
+    want = 1 - (1 - J ** r) ** b
+    hits = int(flags[1::2].sum())
+    assert _binom_ok(hits, pairs, want), (hits / pairs, want)
+    # The first of each pair has no earlier similar document.
+    assert int(flags[0::2].sum()) <= 3
+
+
+def test_bloom_false_positive_closed_form(oracle):
+    """Insert n random keys into one filter sized for n at p = 1e-5, query 4M
+    fresh keys: the hit rate must match (1 - e^{-kn/m})^k."""
+    n = 10_000
+    ix = oracle.OracleIndex(11, 11, 1, n_expected=n, fp_rate=1e-5)
+    rnd = np.random.default_rng(12)
+    keys = rnd.integers(0, 2**63, size=n, dtype=np.uint64) * np.uint64(2) + np.uint64(1)
+    ix.insert_keys(0, keys)
+    assert ix.query_keys(0, keys).all()  # no false negatives
+    fresh = rnd.integers(0, 2**63, size=4_000_000, dtype=np.uint64) * np.uint64(2)
+    fp = int(ix.query_keys(0, fresh).sum())
+    m, k = ix.m, ix.k
+    want = (1 - math.exp(-k * n / m)) ** k
+    lam = want * fresh.size
+    assert abs(fp - lam) <= 4 * math.sqrt(lam) + 2, (fp, lam)
+    # The filter fill matches 1 - e^{-kn/m} as well.
+    fill = ix.popcount(0) / m
+    assert abs(fill - (1 - math.exp(-k * n / m))) < 0.01
+
+
+def test_no_false_negatives_against_exact_band_buckets(oracle):
+    """Replay the stream against an exact band-bucket index (hash maps of the
+    r-row bands, as MinHashLSH stores them) fed with the documents the oracle
+    inserted.  Every document with an exact band match must be flagged, and
+    flags without one must be rare."""
+    from synth import corpus
+    spec = corpus.CorpusSpec(n_docs=3000, seed=4, length_median=120, length_min=10,
+                             length_max=800, dup_frac=0.3, dup_lo=0.0, dup_hi=0.1)
+    off, toks = corpus.generate(spec)
+    P, b, r = 121, 11, 11
+    ix = oracle.OracleIndex(P, b, r, n_expected=3000, fp_rate=1e-4, ngram=5, seed=1)
+    flags = ix.dedup(off, toks)
+    sigs = oracle.batch_signatures(off, toks, 5, ix.a, ix.b)
+    buckets = [set() for _ in range(b)]
+    exact = np.zeros(len(flags), bool)
+    for i in range(len(flags)):
+        bands = [tuple(sigs[i, j * r:(j + 1) * r].tolist()) for j in range(b)]
+        exact[i] = any(bands[j] in buckets[j] for j in range(b))
+        if not flags[i]:
+            for j in range(b):
+                buckets[j].add(bands[j])
+    assert np.all(flags[exact] == 1)
+    extra = int(np.sum(flags.astype(bool) & ~exact))
+    # p_eff = 1 - (1 - 1e-4)^11 ~ 1.1e-3 per document at full load.
+    assert extra <= 12, extra
+    assert exact.sum() > 300  # the planted duplicates are found
+
+
+def test_identical_documents_stream(oracle):
+    doc = np.arange(100, 400, dtype=np.uint32)
+    off, toks = _csr([doc] * 6)
+    ix = oracle.OracleIndex(121, 11, 11)
+    assert ix.dedup(off, toks).tolist() == [0, 1, 1, 1, 1, 1]
+    # A second call continues the same stream.
+    assert ix.dedup(off, toks).tolist() == [1] * 6
+    assert ix.docs_seen == 12
+
+
+def test_query_before_insert_and_modes(oracle):
+    """A document never matches itself (query comes first); with insert-all a
+    duplicate's bits are still inserted, which the default mode skips."""
+    A = np.arange(0, 300, dtype=np.uint32)
+    B = np.arange(10_000, 10_300, dtype=np.uint32)
+    off, toks = _csr([A, A, B])
+    for insert_all in (False, True):
+        ix = oracle.OracleIndex(121, 11, 11, insert_all=insert_all)
+        assert ix.dedup(off, toks).tolist() == [0, 1, 0]
+    # Filters after [A, A]: identical for both modes (A's bits either way).
+    ix1 = oracle.OracleIndex(121, 11, 11)
+    ix2 = oracle.OracleIndex(121, 11, 11, insert_all=True)
+    off2, toks2 = _csr([A, A])
+    ix1.dedup(off2, toks2)
+    ix2.dedup(off2, toks2)
+    for j in range(11):
+        assert np.array_equal(ix1.filter_bytes(j), ix2.filter_bytes(j))
+        assert ix1.popcount(j) <= 17
+
+
+def test_empty_and_short_documents(oracle):
+    """Readings: an empty document has no shingle (all-max signature), so a
+    second empty document is a duplicate of the first; a document shorter than
+    n has one shingle made of all its tokens."""
+    e = np.zeros(0, np.uint32)
+    s3 = np.array([5, 6, 7], np.uint32)
+    off, toks = _csr([e, s3, e, s3, np.array([5, 6, 7, 8], np.uint32)])
+    ix = oracle.OracleIndex(121, 11, 11, ngram=5)
+    assert ix.dedup(off, toks).tolist() == [0, 0, 1, 1, 0]
+
+
+def test_filters_fill_monotonically(oracle):
+    from synth import corpus
+    spec = corpus.CorpusSpec(n_docs=400, seed=9, length_median=80, length_min=5,
+                             length_max=300)
+    off, toks = corpus.generate(spec)
+    ix = oracle.OracleIndex(121, 11, 11, n_expected=400)
+    prev = [0] * 11
+    for s in range(0, 400, 50):
+        sub = off[s:s + 51] - off[s]
+        ix.dedup(sub, toks[int(off[s]):int(off[min(s + 50, 400)])])
+        cur = [ix.popcount(j) for j in range(11)]
+        assert all(c >= p for c, p in zip(cur, prev))
+        prev = cur
+
+
+def test_batch_split_does_not_change_flags(oracle):
+    """The stream semantics do not depend on how the stream is cut into calls."""
+    from synth import corpus
+    spec = corpus.CorpusSpec(n_docs=600, seed=2, length_median=60, length_min=3,
+                             length_max=300, dup_frac=0.4, dup_lo=0.0, dup_hi=0.05)
+    off, toks = corpus.generate(spec)
+    whole = oracle.OracleIndex(121, 11, 11, n_expected=600).dedup(off, toks)
+    ix = oracle.OracleIndex(121, 11, 11, n_expected=600)
+    parts = []
+    for s, e in [(0, 1), (1, 250), (250, 251), (251, 600)]:
+        parts.append(ix.dedup(off[s:e + 1], toks))
+    assert np.array_equal(np.concatenate(parts), whole)
+    assert whole.sum() > 100
