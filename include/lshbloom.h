@@ -1,0 +1,199 @@
+/*
+ * lshbloom.h -- C ABI of the GB300 LSHBloom deduplication library.
+ *
+ * LSHBloom (arxiv 2411.04257) decides, for each document of a stream, whether
+ * it is a near-duplicate of an earlier one.  A document is a set of word
+ * n-grams (Sec. 2.2); its MinHash signature holds, for each of P universal
+ * hash permutations, the minimum permuted shingle hash (Sec. 2.2, Sec. 4.1);
+ * the signature's first b*r rows form b bands of r rows, each reduced to one
+ * integer key by summation (Sec. 4.1); each band key is queried in, and then
+ * inserted into, that band's Bloom filter (Sec. 4.1, Sec. 4.2).  A document is
+ * a duplicate when any band's key is found (Sec. 4.2).  Documents are judged
+ * in stream order against every earlier document (Sec. 2.1, Sec. 4.4.2).
+ *
+ * Conventions fixed by this library where the paper names none (the CPU
+ * reference implements the same conventions independently):
+ *   - shingle hash: SHA-1 (FIPS 180-4) of the n tokens as little-endian
+ *     uint32 bytes, first four digest bytes as a little-endian uint32
+ *     (Sec. 4.1 names SHA1; Sec. 4.3 32-bit hash values);
+ *   - a document of 0 < L < n tokens has one shingle of all L tokens; an
+ *     empty document has none and keeps the all-(2^32-1) signature;
+ *   - permutation i: ((a_i h + b_i) mod (2^61 - 1)) mod 2^32, exact on the
+ *     93-bit product; (a_i, b_i) drawn from a SplitMix64 stream of `seed` in
+ *     the order a_0, b_0, a_1, ...: a = 1 + x mod (2^61 - 2), b = x mod (2^61 - 1);
+ *   - band key j: sum of rows j*r .. j*r+r-1, modulo 2^64;
+ *   - probes: x = mix64(key ^ j*0x9e3779b97f4a7c15), y = mix64(x ^
+ *     0x6a09e667f3bcc909) | 1, q_u = high64((x + u*y) * m), u < k
+ *     (Kirsch-Mitzenmacher double hashing; mix64 is the SplitMix64 finaliser);
+ *   - filter size m = ceil(-n ln p / (ln 2)^2) rounded up to a multiple of 256
+ *     bits (Sec. 4.5), k = max(1, round(m/n ln 2)); p_eff splits as
+ *     p = 1 - (1 - p_eff)^(1/b) (Sec. 4.3);
+ *   - insert rule: by default only documents judged not duplicate are
+ *     inserted (Sec. 4.4.2); LSHB_INSERT_ALL inserts every document.
+ *
+ * Threading: calls on one handle are serialised by the handle.  Different
+ * handles are independent.  All functions return an lshb_status; on failure
+ * lshbloom_last_error() gives a message for the calling thread.  A call that
+ * fails argument or CSR validation changes no state.
+ *
+ * Memory: pointers marked "host or device" may point to host memory (pageable
+ * or pinned) or to device memory of the handle's GPU; the library finds out
+ * which with cudaPointerGetAttributes and copies as needed.  The caller owns
+ * all buffers it passes; the handle owns its filters and scratch.
+ *
+ * CSR batches: document d of a batch of D documents is
+ * tokens[offsets[d] .. offsets[d+1]-1]; offsets has D+1 non-decreasing
+ * entries (offsets[0] need not be 0); tokens holds uint32 word hashes.
+ */
+#ifndef LSHBLOOM_H
+#define LSHBLOOM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LSHB_API __attribute__((visibility("default")))
+#else
+#define LSHB_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lshbloom lshbloom_t;
+
+typedef enum {
+    LSHB_OK = 0,
+    LSHB_ERR_ARG = -1,     /* bad argument or parameter combination */
+    LSHB_ERR_CSR = -2,     /* offsets not non-decreasing */
+    LSHB_ERR_OOM = -3,     /* device or host allocation failed */
+    LSHB_ERR_CUDA = -4,    /* a CUDA call failed */
+    LSHB_ERR_TIMEOUT = -5, /* a bounded device wait ran out */
+    LSHB_ERR_IO = -6,      /* file read/write failed or bad file */
+    LSHB_ERR_BUSY = -7     /* no admission slot / memory (serving) */
+} lshb_status;
+
+typedef enum { LSHB_INSERT_NONDUP = 0, LSHB_INSERT_ALL = 1 } lshb_insert_mode;
+
+typedef enum {
+    LSHB_EXEC_PLAIN = 0,   /* one kernel per stage */
+    LSHB_EXEC_BATCHED = 1  /* persistent fused kernel over a work queue, graph-launched */
+} lshb_exec_mode;
+
+typedef struct {
+    uint32_t num_perm;        /* P, >= 1, <= 1024 */
+    uint32_t bands;           /* b, >= 1, <= 64 */
+    uint32_t rows;            /* r, >= 1, b*r <= P */
+    uint32_t ngram;           /* n, word n-gram size, 1..64 (default 5) */
+    uint64_t n_expected;      /* documents the filters are sized for, >= 1 */
+    double fp_rate;           /* per-filter p in (0,1), or p_eff if fp_is_effective */
+    int32_t fp_is_effective;  /* nonzero: fp_rate is p_eff over all b filters */
+    uint32_t insert_mode;     /* lshb_insert_mode */
+    uint64_t seed;            /* permutation coefficient seed (default 1) */
+    const uint64_t *perm_a;   /* optional host array[P] of a_i in [1, 2^61-2] */
+    const uint64_t *perm_b;   /* optional host array[P] of b_i in [0, 2^61-2] */
+    uint32_t exec_mode;       /* lshb_exec_mode (default BATCHED) */
+    int32_t device;           /* CUDA device ordinal, -1 = current */
+    uint64_t max_batch_docs;  /* docs per internal chunk, 0 = default (262144) */
+    uint64_t max_batch_tokens;/* tokens per internal chunk, 0 = default (2^28) */
+    uint32_t item_shingles;   /* batched mode: shingles per work item, 0 = autotuned */
+    uint32_t reserved[7];
+} lshb_config;
+
+typedef struct {
+    uint32_t num_perm, bands, rows, ngram, k, insert_mode, exec_mode, item_shingles;
+    uint64_t m_bits;          /* bits per filter */
+    uint64_t filter_bytes;    /* bytes per filter as stored (m_bits / 8) */
+    uint64_t docs_seen;       /* documents judged so far */
+    uint64_t dups_seen;       /* of which duplicates */
+    double fp_rate;           /* per-filter p actually used */
+    double fill[64];          /* fraction of set bits per filter (first `bands`) */
+    uint64_t resolve_rounds;  /* in-batch order-resolution iterations so far */
+    uint64_t uncertain_docs;  /* documents that needed in-batch resolution */
+} lshb_stats;
+
+/* Fill *cfg with defaults: P=121, b=11, r=11, n=5, n_expected=10000,
+ * fp_rate=1e-5 (per filter), seed=1, INSERT_NONDUP, BATCHED, device -1. */
+LSHB_API void lshbloom_config_default(lshb_config *cfg);
+
+/* Create an index of b Bloom filters sized for n_expected documents at
+ * per-filter false-positive rate fp_rate (Sec. 4.5 sizing; Sec. 4.1: one
+ * filter per band).  Other settings take lshbloom_config_default values.
+ * *out receives the handle.  Errors: ERR_ARG (b*r > P, fp not in (0,1),
+ * n_expected = 0, out NULL), ERR_OOM, ERR_CUDA. */
+LSHB_API lshb_status lshbloom_create(uint32_t P, uint32_t b, uint32_t r, uint64_t n_expected,
+                            double fp_rate, lshbloom_t **out);
+
+/* Create from a full configuration (see lshb_config).  Errors as above. */
+LSHB_API lshb_status lshbloom_create_ex(const lshb_config *cfg, lshbloom_t **out);
+
+/* Judge D documents in stream order against all earlier documents of this
+ * handle (Sec. 2.1, Sec. 4.2) and insert them (Sec. 4.1, Sec. 4.4.2).
+ * offsets: host or device uint64[D+1]; tokens: host or device uint32, indexed
+ * by offsets; flags_out: host or device uint8[D], 1 = duplicate.  Returns
+ * when flags_out is written.  D = 0 is a no-op.  Errors: ERR_ARG (NULL
+ * pointer with D > 0), ERR_CSR (offsets decreasing; no state changed),
+ * ERR_OOM, ERR_CUDA, ERR_TIMEOUT. */
+LSHB_API lshb_status lshbloom_dedup(lshbloom_t *h, const uint64_t *offsets, const uint32_t *tokens,
+                           uint64_t D, uint8_t *flags_out);
+
+/* As lshbloom_dedup with device pointers only, ordered on `stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  The host may block while
+ * it plans chunks and when a batch needs in-batch order resolution; flags_out
+ * is complete when the stream reaches the end of the enqueued work. */
+LSHB_API lshb_status lshbloom_dedup_async(lshbloom_t *h, const uint64_t *offsets, const uint32_t *tokens,
+                                 uint64_t D, uint8_t *flags_out, void *stream);
+
+/* MinHash signatures of D documents (Sec. 2.2, Sec. 4.1), without touching the
+ * filters.  sig_out: host or device uint32[D][P], row-major.  Errors as for
+ * lshbloom_dedup. */
+LSHB_API lshb_status lshbloom_signatures(lshbloom_t *h, const uint64_t *offsets, const uint32_t *tokens,
+                                uint64_t D, uint32_t *sig_out);
+
+/* Band keys of D documents (Sec. 4.1), without touching the filters.
+ * keys_out: host or device uint64[D][b], row-major. */
+LSHB_API lshb_status lshbloom_band_keys(lshbloom_t *h, const uint64_t *offsets, const uint32_t *tokens,
+                               uint64_t D, uint64_t *keys_out);
+
+/* Shingle hashes (Sec. 4.1 base hash) of D documents: for document d,
+ * h_out[offsets[d] - offsets[0] + s] is the hash of shingle s for
+ * s < shingles(d); the other n-1 entries of each document are 0.
+ * h_out: host or device uint32[offsets[D] - offsets[0]]. */
+LSHB_API lshb_status lshbloom_shingle_hashes(lshbloom_t *h, const uint64_t *offsets,
+                                    const uint32_t *tokens, uint64_t D, uint32_t *h_out);
+
+/* Copy the permutation coefficients (host uint64[P] each). */
+LSHB_API lshb_status lshbloom_coefficients(const lshbloom_t *h, uint64_t *a_out, uint64_t *b_out);
+
+/* Copy filter `band` to host memory: ceil(m/8) bytes, bit q of the filter at
+ * byte q/8, bit q%8 (least significant first). */
+LSHB_API lshb_status lshbloom_filter_bytes(lshbloom_t *h, uint32_t band, uint8_t *host_out);
+
+/* Clear every filter and the document counters. */
+LSHB_API lshb_status lshbloom_reset(lshbloom_t *h);
+
+/* Sizes, counters and per-filter fill. */
+LSHB_API lshb_status lshbloom_stats(lshbloom_t *h, lshb_stats *out);
+
+/* Write the index (a header with every parameter and counter, then the b
+ * filters) to `path`; load it back into a new handle on the current (or
+ * `device` >= 0) GPU.  A loaded index continues the stream exactly. */
+LSHB_API lshb_status lshbloom_save(lshbloom_t *h, const char *path);
+LSHB_API lshb_status lshbloom_load(const char *path, int32_t device, lshbloom_t **out);
+
+/* (b, r) with b*r <= P minimising the equal-weight sum of the LSH false
+ * positive and false negative integrals at threshold T (Eqs. 1-2, Sec. 4.3). */
+LSHB_API lshb_status lshbloom_optimal_br(double T, uint32_t P, uint32_t *b_out, uint32_t *r_out);
+
+/* Message of the last failed call on this thread ("" if none). */
+LSHB_API const char *lshbloom_last_error(void);
+
+/* Release the handle and everything it owns.  NULL is a no-op. */
+LSHB_API void lshbloom_destroy(lshbloom_t *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSHBLOOM_H */

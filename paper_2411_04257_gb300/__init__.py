@@ -1,0 +1,228 @@
+"""GB300 LSHBloom: near-duplicate detection with MinHash LSH bands indexed by
+Bloom filters (arxiv 2411.04257), on hand-written sm_103a CUDA kernels.
+
+The Python layer only marshals arguments to the C ABI of liblshbloom.so
+(include/lshbloom.h).  Inputs may be numpy arrays (host), or torch tensors on
+the host or on the handle's GPU; outputs live where the tokens live.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from ._native import (EXEC_BATCHED, EXEC_PLAIN, INSERT_ALL, INSERT_NONDUP, Config,
+                      LSHBloomError, Stats, check, lib)
+
+__all__ = ["LSHBloom", "LSHBloomError", "optimal_br", "lib", "EXEC_PLAIN", "EXEC_BATCHED"]
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _arg(x, np_dtype, torch_dtypes):
+    """(pointer, keep-alive object, is_cuda) for a 1-D/2-D array argument."""
+    if _is_torch(x):
+        import torch
+        if x.dtype not in [getattr(torch, d) for d in torch_dtypes if hasattr(torch, d)]:
+            raise TypeError(f"expected one of {torch_dtypes}, got {x.dtype}")
+        if not x.is_contiguous():
+            x = x.contiguous()
+        return x.data_ptr(), x, x.is_cuda
+    a = np.ascontiguousarray(x)
+    if a.dtype != np_dtype:
+        if a.dtype.kind in "iu" and a.dtype.itemsize == np.dtype(np_dtype).itemsize:
+            a = a.view(np_dtype)
+        else:
+            a = a.astype(np_dtype)
+    return a.ctypes.data, a, False
+
+
+def _out(n_items, row, np_dtype, torch_dtype, like_cuda_tensor):
+    if like_cuda_tensor is not None:
+        import torch
+        shape = (n_items,) if row is None else (n_items, row)
+        t = torch.empty(shape, dtype=getattr(torch, torch_dtype), device=like_cuda_tensor.device)
+        return t.data_ptr(), t
+    shape = (n_items,) if row is None else (n_items, row)
+    a = np.empty(shape, dtype=np_dtype)
+    return a.ctypes.data, a
+
+
+class LSHBloom:
+    """b Bloom filters, one per LSH band, fed in stream order.
+
+    Parameters follow lshb_config: P permutations, b bands of r rows, n-gram
+    size, the number of documents the filters are sized for and their
+    false-positive rate (per filter, or effective over all b when
+    fp_is_effective)."""
+
+    def __init__(self, P: int = 121, bands: int = 11, rows: int = 11, n_expected: int = 10_000,
+                 fp_rate: float = 1e-5, ngram: int = 5, seed: int = 1, insert_all: bool = False,
+                 fp_is_effective: bool = False, exec_mode: str = "batched", device: int = -1,
+                 max_batch_docs: int = 0, max_batch_tokens: int = 0, item_shingles: int = 0,
+                 perm_a=None, perm_b=None, _handle=None):
+        self._h = None
+        if _handle is not None:
+            self._h = _handle
+            return
+        cfg = Config()
+        lib().lshbloom_config_default(C.byref(cfg))
+        cfg.num_perm, cfg.bands, cfg.rows, cfg.ngram = P, bands, rows, ngram
+        cfg.n_expected, cfg.fp_rate = n_expected, fp_rate
+        cfg.fp_is_effective = 1 if fp_is_effective else 0
+        cfg.insert_mode = INSERT_ALL if insert_all else INSERT_NONDUP
+        cfg.seed = seed
+        cfg.exec_mode = {"plain": EXEC_PLAIN, "batched": EXEC_BATCHED}[exec_mode]
+        cfg.device = device
+        cfg.max_batch_docs, cfg.max_batch_tokens = max_batch_docs, max_batch_tokens
+        cfg.item_shingles = item_shingles
+        keep = []
+        if perm_a is not None:
+            pa = np.ascontiguousarray(perm_a, np.uint64)
+            pb = np.ascontiguousarray(perm_b, np.uint64)
+            keep += [pa, pb]
+            cfg.perm_a = pa.ctypes.data_as(C.POINTER(C.c_uint64))
+            cfg.perm_b = pb.ctypes.data_as(C.POINTER(C.c_uint64))
+        h = C.c_void_p()
+        check(lib().lshbloom_create_ex(C.byref(cfg), C.byref(h)))
+        self._h = h
+
+    # -- lifetime ---------------------------------------------------------------
+    def close(self) -> None:
+        if self._h:
+            lib().lshbloom_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    # -- the path ---------------------------------------------------------------
+    def _inputs(self, offsets, tokens):
+        po, ko, co = _arg(offsets, np.uint64, ["uint64", "int64"])
+        pt, kt, ct = _arg(tokens, np.uint32, ["uint32", "int32"])
+        D = (ko.shape[0] if hasattr(ko, "shape") else len(ko)) - 1
+        like = kt if ct else None
+        return po, pt, max(D, 0), like, (ko, kt)
+
+    def dedup(self, offsets, tokens, out=None):
+        """uint8 duplicate flags of the batch (Sec. 2.1 decision), inserting it."""
+        po, pt, D, like, keep = self._inputs(offsets, tokens)
+        if out is None:
+            pf, fl = _out(D, None, np.uint8, "uint8", like)
+        else:
+            pf, fl, _ = _arg(out, np.uint8, ["uint8"])
+        check(lib().lshbloom_dedup(self._h, po, pt, D, pf))
+        return fl
+
+    def dedup_async(self, offsets, tokens, stream=None):
+        """As dedup, device tensors only, ordered on `stream` (torch stream or
+        raw cudaStream_t; default the current torch stream)."""
+        import torch
+        po, pt, D, like, keep = self._inputs(offsets, tokens)
+        pf, fl = _out(D, None, np.uint8, "uint8", like)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        check(lib().lshbloom_dedup_async(self._h, po, pt, D, pf, C.c_void_p(sp)))
+        return fl
+
+    def signatures(self, offsets, tokens):
+        po, pt, D, like, keep = self._inputs(offsets, tokens)
+        ps, sig = _out(D, self.P, np.uint32, "uint32", like)
+        check(lib().lshbloom_signatures(self._h, po, pt, D, ps))
+        return sig
+
+    def band_keys(self, offsets, tokens):
+        po, pt, D, like, keep = self._inputs(offsets, tokens)
+        pk, keys = _out(D, self.bands, np.uint64, "uint64", like)
+        check(lib().lshbloom_band_keys(self._h, po, pt, D, pk))
+        return keys
+
+    def shingle_hashes(self, offsets, tokens):
+        po, pt, D, like, keep = self._inputs(offsets, tokens)
+        ko = keep[0]
+        n = int(ko[-1]) - int(ko[0]) if D > 0 else 0
+        ph, hs = _out(n, None, np.uint32, "uint32", like)
+        check(lib().lshbloom_shingle_hashes(self._h, po, pt, D, ph))
+        return hs
+
+    # -- inspection ---------------------------------------------------------------
+    def stats(self) -> dict:
+        s = Stats()
+        check(lib().lshbloom_stats(self._h, C.byref(s)))
+        d = {f: getattr(s, f) for f, _ in Stats._fields_ if f != "fill"}
+        d["fill"] = list(s.fill)[: s.bands]
+        return d
+
+    def _dims(self):
+        if not hasattr(self, "_dim_cache"):
+            s = self.stats()
+            self._dim_cache = (s["num_perm"], s["bands"], s["rows"], s["m_bits"], s["k"])
+        return self._dim_cache
+
+    @property
+    def P(self) -> int:
+        return self._dims()[0]
+
+    @property
+    def bands(self) -> int:
+        return self._dims()[1]
+
+    @property
+    def rows(self) -> int:
+        return self._dims()[2]
+
+    @property
+    def m(self) -> int:
+        return self._dims()[3]
+
+    @property
+    def k(self) -> int:
+        return self._dims()[4]
+
+    def coefficients(self):
+        P = self.P
+        a = np.zeros(P, np.uint64)
+        b = np.zeros(P, np.uint64)
+        check(lib().lshbloom_coefficients(self._h, a.ctypes.data, b.ctypes.data))
+        return a, b
+
+    def filter_bytes(self, band: int) -> np.ndarray:
+        out = np.zeros((self.m + 7) // 8, np.uint8)
+        check(lib().lshbloom_filter_bytes(self._h, band, out.ctypes.data))
+        return out
+
+    def reset(self) -> None:
+        check(lib().lshbloom_reset(self._h))
+
+    def save(self, path: str) -> None:
+        check(lib().lshbloom_save(self._h, path.encode()))
+
+    @classmethod
+    def load(cls, path: str, device: int = -1) -> "LSHBloom":
+        h = C.c_void_p()
+        check(lib().lshbloom_load(path.encode(), device, C.byref(h)))
+        return cls(_handle=h)
+
+
+def optimal_br(T: float, P: int):
+    """(b, r) minimising the equal-weight LSH error integrals (Eqs. 1-2)."""
+    b = C.c_uint32()
+    r = C.c_uint32()
+    check(lib().lshbloom_optimal_br(T, P, C.byref(b), C.byref(r)))
+    return int(b.value), int(r.value)

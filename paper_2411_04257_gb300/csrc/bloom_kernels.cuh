@@ -1,0 +1,55 @@
+// Bloom-stage kernel arguments and launch wrappers.
+#pragma once
+
+#include "lshb_device.cuh"
+#include "lshb_internal.h"
+
+namespace lshb {
+
+constexpr uint32_t kErrTableFull = 1u;   // resolution table overflowed
+constexpr uint32_t kErrQueue = 2u;       // persistent kernel work-queue inconsistency
+
+struct BloomArgs {
+    uint64_t D;
+    uint32_t bands, k;
+    uint64_t m_bits, words_per_filter;
+    uint32_t *filters;          // bands x words_per_filter
+    const uint64_t *keys;       // D x bands
+    uint64_t *miss;             // D x bands: bit u set when probe u found a clear bit
+    uint32_t *sketch1, *sketch2;
+    uint32_t sketch_bits_log2;
+    uint8_t *status;            // D: 1 duplicate whatever the order, 2 uncertain, 0 not duplicate
+    uint64_t *cand;             // D: candidate bands
+    uint8_t *prehit;            // D
+    uint32_t *error;            // device error word
+};
+
+struct ResolveTable {
+    uint64_t *keys;             // global bit ids, ~0 = empty
+    uint32_t mask;              // capacity - 1 (power of two)
+    uint32_t *first_fixed;      // earliest order-independent setter per slot
+    uint32_t *first;            // earliest inserted setter per slot, this sweep
+    uint32_t *slots;            // nu x bands x k slot ids (~0 = none)
+    uint8_t *ins;               // nu: inserted in the current sweep
+    uint8_t *udup;              // nu: duplicate in the current sweep
+    uint32_t *changed;
+};
+
+cudaError_t launch_probe_mark(const BloomArgs &a, cudaStream_t s);
+cudaError_t launch_classify(const BloomArgs &a, uint32_t *block_counts, uint32_t *total,
+                            uint32_t *ulist, cudaStream_t s);
+cudaError_t launch_count_keys(const BloomArgs &a, const uint32_t *ulist, uint32_t nu,
+                              unsigned long long *count, cudaStream_t s);
+cudaError_t launch_resolve_setup(const BloomArgs &a, const uint32_t *ulist, uint32_t nu,
+                                 const ResolveTable &t, int insert_all, cudaStream_t s);
+cudaError_t launch_resolve_iteration(const BloomArgs &a, const uint32_t *ulist, uint32_t nu,
+                                     const ResolveTable &t, int insert_all, cudaStream_t s);
+cudaError_t launch_resolve_sequential(const BloomArgs &a, const uint32_t *ulist, uint32_t nu,
+                                      const ResolveTable &t, cudaStream_t s);
+cudaError_t launch_finalize_insert(const BloomArgs &a, const uint32_t *ulist, uint32_t nu,
+                                   const ResolveTable &t, int insert_all, uint8_t *flags,
+                                   uint8_t *insd, unsigned long long *dup_count, cudaStream_t s);
+cudaError_t launch_popcount(const uint32_t *words, uint64_t n, unsigned long long *out,
+                            cudaStream_t s);
+
+}  // namespace lshb

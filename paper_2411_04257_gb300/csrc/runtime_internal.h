@@ -1,0 +1,113 @@
+// Host-side state of a handle and the runtime's internal entry points.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "../../include/lshbloom.h"
+#include "bloom_kernels.cuh"
+#include "lshb_internal.h"
+
+namespace lshb {
+
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    lshb_status reserve(size_t want);  // grow-only; contents are not kept
+    void release();
+};
+
+enum BufId {
+    B_KEYS, B_MISS, B_CAND, B_STATUS, B_PREHIT, B_FLAGS, B_INSD, B_ULIST, B_BLOCKCNT, B_OFFSTAGE,
+    B_SIG, B_HASHES, B_SKETCH1, B_SKETCH2, B_HT_KEYS, B_HT_FIXED, B_HT_FIRST, B_HT_SLOTS,
+    B_HT_INS, B_HT_UDUP, B_HASHOUT, B_OUTSTAGE, B_ITEMS, B_PENDING, B_NBUF
+};
+
+// Slots of the small device counter block (uint32 units).
+enum CounterId {
+    C_NU = 0,         // uncertain documents of the chunk
+    C_CHANGED = 1,    // a resolution sweep changed an insert decision
+    C_ERROR = 2,      // device error bits
+    C_KEYCOUNT = 4,   // (u64) candidate bits of uncertain documents
+    C_DUPCOUNT = 6,   // (u64) duplicates of the chunk
+    C_POPCOUNT = 8,   // (u64) popcount scratch
+    C_QUEUE = 10      // (u64) batched work-queue head
+};
+
+struct SigPass {
+    uint32_t p0, npc;
+    int pc;
+    PermSlice c;
+};
+
+struct ChunkIn {
+    const uint64_t *offsets = nullptr;  // device, D+1
+    const uint32_t *tokens = nullptr;   // device; document d starts at offsets[d] - tok_base
+    uint64_t tok_base = 0;
+    uint64_t D = 0;
+};
+
+struct BatchedState;
+
+}  // namespace lshb
+
+struct lshbloom {
+    std::mutex mu;
+    lshb_config cfg{};
+    int device = -1;
+    uint32_t P = 0, bands = 0, rows = 0, ngram = 0, k = 0;
+    bool insert_all = false;
+    double p = 0.0;
+    uint64_t m = 0, words_per_filter = 0;
+    std::vector<uint64_t> a, b;
+    std::vector<lshb::SigPass> passes;
+    uint32_t *filters = nullptr;
+    cudaStream_t stream = nullptr, copy_stream = nullptr;
+    cudaEvent_t ev_stage_free[2] = {nullptr, nullptr};
+    cudaEvent_t ev_stage_ready[2] = {nullptr, nullptr};
+    lshb::DevBuf stage_tok[2];
+    uint32_t *host_stage_tok[2] = {nullptr, nullptr};
+    uint32_t *counters = nullptr;       // device, 64 x uint32
+    uint32_t *host_counters = nullptr;  // pinned mirror
+    lshb::DevBuf bufs[lshb::B_NBUF];
+    uint64_t max_docs = 0, max_tokens = 0;
+    uint32_t sketch_log2_cap = 0;
+    uint32_t item_shingles = 0;
+    bool batched_ready = false;
+    lshb::BatchedState *batched = nullptr;
+    uint64_t docs_seen = 0, dups_seen = 0, resolve_rounds = 0, uncertain_docs = 0;
+
+    lshb::DevBuf &buf(lshb::BufId id) { return bufs[id]; }
+    ~lshbloom();
+};
+
+namespace lshb {
+
+lshb_status fail(lshb_status st, const char *fmt, ...);
+lshb_status cuda_fail(cudaError_t e, const char *what);
+lshb_status init_handle(lshbloom *h, const lshb_config *cfg);
+bool is_device_pointer(const void *p);
+lshb_status host_offsets(lshbloom *h, const uint64_t *offsets, uint64_t D, bool dev,
+                         std::vector<uint64_t> &out);
+void plan_chunks(const lshbloom *h, const std::vector<uint64_t> &off, bool bound_tokens,
+                 std::vector<std::pair<uint64_t, uint64_t>> &chunks);
+lshb_status ensure_chunk_scratch(lshbloom *h, uint64_t Dc, uint64_t Tc, bool plain_hashes,
+                                 bool need_sig);
+lshb_status ensure_stage(lshbloom *h, uint64_t Tc);
+lshb_status run_signatures(lshbloom *h, const ChunkIn &in, uint32_t *sig_out, uint32_t *hash_out,
+                           bool want_keys, cudaStream_t s);
+BloomArgs bloom_args(lshbloom *h, uint64_t D);
+lshb_status run_bloom(lshbloom *h, uint64_t D, uint8_t *flags_dev, cudaStream_t s);
+
+// Batched (persistent, graph-launched) form.
+lshb_status run_batched(lshbloom *h, const uint64_t *offsets, const uint32_t *tokens, uint64_t D,
+                        uint8_t *flags, const std::vector<uint64_t> &off, bool off_dev,
+                        bool tok_dev, bool out_dev, cudaStream_t s);
+void destroy_batched_state(lshbloom *h);
+
+}  // namespace lshb

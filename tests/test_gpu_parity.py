@@ -1,0 +1,215 @@
+"""GPU path against the CPU oracle, element by element, through the C ABI.
+
+Everything here is integer work, so the bar is bit-exact: shingle hashes,
+signatures, band keys, duplicate flags and the final filter bits."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lshb():
+    import paper_2411_04257_gb300 as L
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    L.lib()
+    return L
+
+
+@pytest.fixture(scope="module")
+def corpus():
+    from synth import corpus as C
+    return C
+
+
+def _dev(off, tok):
+    return (torch.from_numpy(np.ascontiguousarray(off).view(np.int64)).cuda(),
+            torch.from_numpy(np.ascontiguousarray(tok).view(np.int32)).cuda())
+
+
+def _csr(docs):
+    lens = np.array([len(d) for d in docs], np.uint64)
+    off = np.zeros(len(docs) + 1, np.uint64)
+    np.cumsum(lens, out=off[1:])
+    tok = np.concatenate([np.asarray(d, np.uint32) for d in docs]) if docs else np.zeros(0, np.uint32)
+    return off, tok
+
+
+def _small_corpus(corpus, n=700, seed=5, **kw):
+    args = dict(n_docs=n, seed=seed, length_median=150, length_min=0, length_max=3000,
+                dup_frac=0.3, dup_lo=0.0, dup_hi=0.08)
+    args.update(kw)
+    return corpus.generate(corpus.CorpusSpec(**args))
+
+
+@pytest.mark.parametrize("ngram", [5, 1, 3, 7, 14])
+def test_shingle_hashes(lshb, oracle, corpus, ngram):
+    off, tok = _small_corpus(corpus, n=300, length_min=0)
+    ix = lshb.LSHBloom(121, 11, 11, ngram=ngram)
+    got = ix.shingle_hashes(*_dev(off, tok)).cpu().numpy().view(np.uint32)
+    want, counts = oracle.batch_shingle_hashes(off, tok, ngram)
+    pos = 0
+    for d in range(len(off) - 1):
+        base = int(off[d])
+        c = int(counts[d])
+        assert np.array_equal(got[base:base + c], want[pos:pos + c]), d
+        pos += c
+
+
+@pytest.mark.parametrize("P,ngram", [(121, 5), (128, 5), (64, 5), (32, 1), (256, 5), (200, 5),
+                                     (48, 7), (121, 1), (121, 3)])
+def test_signatures(lshb, oracle, corpus, P, ngram):
+    off, tok = _small_corpus(corpus, n=400)
+    ix = lshb.LSHBloom(P, 8, 4, ngram=ngram, seed=11)
+    a, b = ix.coefficients()
+    oa, ob = oracle.coefficients(11, P)
+    assert np.array_equal(a, oa) and np.array_equal(b, ob)
+    got = ix.signatures(*_dev(off, tok)).cpu().numpy().view(np.uint32)
+    want = oracle.batch_signatures(off, tok, ngram, a, b)
+    bad = np.nonzero((got != want).any(axis=1))[0]
+    assert bad.size == 0, f"signature rows differ: {bad[:10]}"
+
+
+@pytest.mark.parametrize("exec_mode", ["batched", "plain"])
+def test_band_keys(lshb, oracle, corpus, exec_mode):
+    off, tok = _small_corpus(corpus, n=500)
+    ix = lshb.LSHBloom(121, 11, 11, exec_mode=exec_mode)
+    got = ix.band_keys(*_dev(off, tok)).cpu().numpy().view(np.uint64)
+    sig = oracle.batch_signatures(off, tok, 5, *oracle.coefficients(1, 121))
+    want = np.stack([oracle.band_keys(s, 11, 11) for s in sig])
+    assert np.array_equal(got, want)
+
+
+def _check_dedup(lshb, oracle, off, tok, calls=None, device_inputs=True, **kw):
+    kw.setdefault("n_expected", max(len(off) - 1, 1))
+    okw = {k: v for k, v in kw.items() if k in ("n_expected", "fp_rate", "ngram", "seed",
+                                                  "insert_all", "fp_is_effective")}
+    ix = lshb.LSHBloom(121, 11, 11, **kw)
+    ref = oracle.OracleIndex(121, 11, 11, **okw)
+    D = len(off) - 1
+    cuts = calls or [0, D]
+    got = []
+    for s, e in zip(cuts[:-1], cuts[1:]):
+        o = off[s:e + 1]
+        if device_inputs:
+            got.append(ix.dedup(*_dev(o, tok)).cpu().numpy())
+        else:
+            got.append(np.asarray(ix.dedup(o, tok)))
+    got = np.concatenate(got) if got else np.zeros(0, np.uint8)
+    want = ref.dedup(off, tok)
+    bad = np.nonzero(got != want)[0]
+    assert bad.size == 0, f"{bad.size} flags differ, first {bad[:10]}"
+    for j in range(11):
+        assert np.array_equal(ix.filter_bytes(j), ref.filter_bytes(j)), f"filter {j}"
+    st = ix.stats()
+    assert st["docs_seen"] == D and st["dups_seen"] == int(want.sum())
+    return want, st
+
+
+@pytest.mark.parametrize("exec_mode", ["batched", "plain"])
+@pytest.mark.parametrize("insert_all", [False, True])
+def test_dedup_plain_10k_workload(lshb, oracle, corpus, exec_mode, insert_all):
+    """The 10,000-document workload (Zipf 50k words, lognormal median 400,
+    20% near-duplicates), one call, at its own sizing (n=10k, p=1e-5)."""
+    off, tok = corpus.generate(corpus.plain_10k())
+    want, st = _check_dedup(lshb, oracle, off, tok, n_expected=10_000, fp_rate=1e-5,
+                            exec_mode=exec_mode, insert_all=insert_all)
+    # 5-30% substitutions give shingle Jaccard 0.09-0.63, mostly below the
+    # ~0.8 threshold of b = r = 11: few are flagged, and all of them exactly.
+    assert want.sum() >= 10
+
+
+def test_dedup_many_calls_and_small_chunks(lshb, oracle, corpus):
+    off, tok = _small_corpus(corpus, n=1500, dup_frac=0.5)
+    _check_dedup(lshb, oracle, off, tok, calls=[0, 1, 2, 100, 101, 700, 1500],
+                 max_batch_docs=97, max_batch_tokens=5000)
+
+
+def test_dedup_host_inputs(lshb, oracle, corpus):
+    off, tok = _small_corpus(corpus, n=900)
+    _check_dedup(lshb, oracle, off, tok, device_inputs=False, max_batch_docs=200)
+
+
+def test_identical_documents(lshb, oracle):
+    doc = np.arange(1000, 1600, dtype=np.uint32)
+    off, tok = _csr([doc] * 3000)
+    want, st = _check_dedup(lshb, oracle, off, tok)
+    assert want.tolist() == [0] + [1] * 2999
+
+
+def test_duplicate_chains_in_one_batch(lshb, oracle):
+    """d_{i+1} is a near-copy of d_i: long dependence chains inside one call
+    force many resolution sweeps (or the in-order fallback)."""
+    rnd = np.random.default_rng(3)
+    docs = [rnd.integers(0, 1 << 30, size=400).astype(np.uint32)]
+    for i in range(300):
+        nxt = docs[-1].copy()
+        nxt[rnd.integers(0, 400, size=6)] = rnd.integers(0, 1 << 30, size=6)
+        docs.append(nxt)
+    off, tok = _csr(docs)
+    for insert_all in (False, True):
+        _check_dedup(lshb, oracle, off, tok, insert_all=insert_all, fp_rate=1e-3)
+
+
+def test_empty_short_and_long_documents(lshb, oracle):
+    rnd = np.random.default_rng(9)
+    docs = [np.zeros(0, np.uint32), np.array([1, 2, 3], np.uint32), np.zeros(0, np.uint32),
+            np.array([1, 2, 3], np.uint32), np.array([7], np.uint32),
+            rnd.integers(0, 1 << 31, size=200_000).astype(np.uint32),
+            np.array([7], np.uint32), np.array([1, 2, 3, 4], np.uint32)]
+    docs += [rnd.integers(0, 50, size=rnd.integers(0, 12)).astype(np.uint32) for _ in range(400)]
+    docs.append(docs[5].copy())
+    off, tok = _csr(docs)
+    want, _ = _check_dedup(lshb, oracle, off, tok, n_expected=1000)
+    assert want[2] == 1 and want[3] == 1 and want[6] == 1 and want[-1] == 1
+
+
+@pytest.mark.parametrize("ngram", [1, 7])
+def test_dedup_other_ngrams(lshb, oracle, corpus, ngram):
+    off, tok = _small_corpus(corpus, n=800)
+    _check_dedup(lshb, oracle, off, tok, ngram=ngram)
+
+
+def test_sizing_matches_oracle(lshb, oracle):
+    for n, p, eff in [(10_000, 1e-5, False), (39_000_000, 1e-5, False), (1234, 0.01, False),
+                      (10_000, 1e-10, True), (5_000, 1e-3, True)]:
+        ix = lshb.LSHBloom(121, 11, 11, n_expected=n, fp_rate=p, fp_is_effective=eff)
+        pp = oracle.p_from_effective(p, 11) if eff else p
+        assert (ix.m, ix.k) == oracle.sizing(n, pp), (n, p)
+        ix.close()
+
+
+def test_save_load_continues_the_stream(lshb, oracle, corpus, tmp_path):
+    off, tok = _small_corpus(corpus, n=1000, dup_frac=0.4)
+    ix = lshb.LSHBloom(121, 11, 11, n_expected=1000)
+    a = ix.dedup(*_dev(off[:501], tok)).cpu().numpy()
+    path = str(tmp_path / "ix.lshb")
+    ix.save(path)
+    ix.close()
+    ix2 = lshb.LSHBloom.load(path)
+    b = ix2.dedup(*_dev(off[500:], tok)).cpu().numpy()
+    ref = oracle.OracleIndex(121, 11, 11, n_expected=1000)
+    want = ref.dedup(off, tok)
+    assert np.array_equal(np.concatenate([a, b]), want)
+    assert ix2.stats()["docs_seen"] == 1000
+
+
+def test_reset_and_errors(lshb, corpus):
+    off, tok = _small_corpus(corpus, n=50)
+    ix = lshb.LSHBloom(121, 11, 11)
+    f1 = ix.dedup(*_dev(off, tok)).cpu().numpy()
+    ix.reset()
+    f2 = ix.dedup(*_dev(off, tok)).cpu().numpy()
+    assert np.array_equal(f1, f2)
+    bad = off.copy()
+    bad[10] = bad[11] + 1
+    with pytest.raises(lshb.LSHBloomError) as e:
+        ix.dedup(*_dev(bad, tok))
+    assert e.value.status == -2
+    assert ix.stats()["docs_seen"] == 50
+    with pytest.raises(lshb.LSHBloomError):
+        lshb.LSHBloom(121, 12, 11)
+    assert ix.dedup(*_dev(off[:1], tok)).numel() == 0
