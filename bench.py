@@ -1,0 +1,330 @@
+"""Throughput of the LSHBloom deduplication path on one GB300 (or N replicas).
+
+A step is one pass of the whole path over one batch: the peS2o-shaped batch
+of 1,000,000 synthetic documents (lognormal median 3,000 tokens, Zipf(1.1)
+over 200k words, 10% near-duplicates at Jaccard 0.6-0.95; 5-gram shingles,
+P=121, b=11, r=11, filters sized for n=39M at p=1e-5), generated in HBM.
+Each step clears the filters and deduplicates the whole batch, so every step
+does the same work.
+
+Prints one JSON line (rank 0).  `value` is docs/s of the batched form with
+inputs resident in HBM; `plain` is the one-kernel-per-stage form on the same
+batch; `e2e` is the same metric through lshbloom_dedup with pinned host
+buffers, host<->device copies inside the timed region.
+
+--impl reference times the CPU oracle (single thread) on a bounded sample of
+the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (spec factory, n_docs, n_expected, fp_rate)
+    "pes2o_1m": ("pes2o_shaped", 1_000_000, 39_000_000, 1e-5),
+    "plain_10k": ("plain_10k", 10_000, 10_000, 1e-5),
+}
+P, BANDS, ROWS, NGRAM = 121, 11, 11, 5
+SM_COUNT = 152
+IMAD_PER_SM_CLK = 64        # 32-bit integer multiply(-add) results per SM per clock
+SM_MAX_MHZ = 2070.0
+IMAD_PER_PERMHASH = 4       # two 32x32->64 products (lo and hi halves) per (a*h + b)
+
+
+def _rank_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def _spec(name, rank):
+    from synth import corpus
+    fac, n, nexp, fp = WORKLOADS[name]
+    spec = getattr(corpus, fac)() if fac == "plain_10k" else getattr(corpus, fac)(n_docs=n)
+    import dataclasses
+    return dataclasses.replace(spec, seed=spec.seed + rank), nexp, fp
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.p = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.p:
+            self.p.terminate()
+            self.p.wait()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[0]) for r in rows if len(r) >= 7 and r[0].strip().replace(".", "").isdigit()]
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for i, n in enumerate(names):
+                if len(r) > 3 + i and "Active" in r[3 + i] and "Not" not in r[3 + i]:
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][1]),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _cpu_baseline(spec, nexp, fp, target_s=12.0):
+    """The oracle as it stands, single-threaded, on a prefix of the workload."""
+    from oracle import oracle
+    from synth import corpus
+    t = corpus.build_tables(spec)
+    n = 16
+    while True:
+        off, tok = corpus.generate(spec, 0, n, tables=t)
+        ix = oracle.OracleIndex(P, BANDS, ROWS, n_expected=nexp, fp_rate=fp, ngram=NGRAM)
+        t0 = time.perf_counter()
+        ix.dedup(off, tok)
+        dt = time.perf_counter() - t0
+        ix.close()
+        if dt > target_s / 4 or n >= spec.n_docs:
+            break
+        n = min(spec.n_docs, max(n * 2, int(n * target_s / max(dt, 1e-3) / 2)))
+    return {"value": n / dt, "unit": "docs/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {n} docs of the workload ({int(off[-1])} tokens), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = _rank_env()
+    if rank != 0:
+        return 0
+    from oracle import oracle
+    from synth import corpus
+    spec, nexp, fp = _spec(args.workload, 0)
+    t = corpus.build_tables(spec)
+    n = args.ref_docs
+    off, tok = corpus.generate(spec, 0, n, tables=t)
+    times = []
+    for i in range(args.warmup + args.steps):
+        ix = oracle.OracleIndex(P, BANDS, ROWS, n_expected=nexp, fp_rate=fp, ngram=NGRAM)
+        t0 = time.perf_counter()
+        ix.dedup(off, tok)
+        dt = time.perf_counter() - t0
+        ix.close()
+        if i >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    v = n * len(times) / total
+    line = {"impl": "reference", "metric": "docs/s (LSHBloom dedup)", "value": v, "unit": "docs/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": args.workload, "sample_docs": n},
+            "cpu_baseline": {"value": v, "unit": "docs/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {n} docs of the workload per step"},
+            "e2e": {"value": v, "unit": "docs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _time_steps(fn, steps, warmup, stream, sync, on_start=None):
+    import torch
+    for _ in range(warmup):
+        fn()
+    sync()
+    if on_start:
+        on_start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    for _ in range(steps):
+        fn()
+    ev[1].record(stream)
+    sync()
+    return ev[0].elapsed_time(ev[1]) / 1e3
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = _rank_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2411_04257_gb300 import LSHBloom
+    from synth import gpu as sgpu
+
+    spec, nexp, fp = _spec(args.workload, rank)
+    gen = sgpu.DeviceCorpus(spec, dev)
+    off, tok = gen.generate(0, spec.n_docs)
+    torch.cuda.synchronize()
+    D = spec.n_docs
+    T = int(off[-1].item())
+    L = (off[1:] - off[:-1])
+    S = torch.where(L >= NGRAM, L - NGRAM + 1, (L > 0).to(L.dtype))
+    shingles = int(S.sum().item())
+    permhashes = shingles * P
+
+    stream = torch.cuda.Stream(dev)
+
+    def barrier_sync():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+
+    results = {}
+    launches = {}
+    stage = {}
+    for mode in (["batched", "plain"] if not args.skip_plain else ["batched"]):
+        ix = LSHBloom(P, BANDS, ROWS, n_expected=nexp, fp_rate=fp, ngram=NGRAM, exec_mode=mode,
+                      device=local)
+
+        def step():
+            ix.reset()
+            with torch.cuda.stream(stream):
+                ix.dedup_async(off, tok, stream=stream)
+
+        s0 = {}
+        with Clocks(local) as ck:
+            dt = _time_steps(step, args.steps, args.warmup, stream, barrier_sync,
+                             on_start=lambda: s0.update(ix.stats()))
+        clocks = ck.summary()
+        s1 = ix.stats()
+        launches[mode] = s1["kernel_launches"] - s0["kernel_launches"]
+        stage[mode] = {"sig_ms": s1["sig_ms"] - s0["sig_ms"],
+                       "bloom_ms": s1["bloom_ms"] - s0["bloom_ms"],
+                       "sig_chunks": s1["sig_chunks"] - s0["sig_chunks"]}
+        t = torch.tensor([dt], device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+        ix.reset()
+        flags = ix.dedup_async(off, tok, stream=stream)
+        torch.cuda.synchronize()
+        results[mode] = {"seconds": dt, "docs_per_s": D * world * args.steps / dt,
+                         "shingle_hashes_per_s": permhashes * world * args.steps / dt,
+                         "clocks": clocks, "dups_per_step": int(flags.sum().item())}
+        ix.close()
+
+    # --- dominant kernel: the signature stage, timed with CUDA events on its
+    # launching stream inside the timed steps (library stage timers) --------
+    sb = stage["batched"]
+    sig_s = sb["sig_ms"] / 1e3 / args.steps          # per step
+    achieved_imad = IMAD_PER_PERMHASH * permhashes / sig_s
+    peak_imad = SM_COUNT * IMAD_PER_SM_CLK * SM_MAX_MHZ * 1e6
+
+    # --- end to end through host buffers --------------------------------------
+    e2e = None
+    if not args.skip_e2e:
+        h_off = torch.empty(D + 1, dtype=torch.int64, pin_memory=True)
+        h_tok = torch.empty(T, dtype=torch.int32, pin_memory=True)
+        h_off.copy_(off)
+        h_tok.copy_(tok)
+        h_flags = torch.empty(D, dtype=torch.uint8, pin_memory=True)
+        ixe = LSHBloom(P, BANDS, ROWS, n_expected=nexp, fp_rate=fp, ngram=NGRAM,
+                       exec_mode="batched", device=local)
+        for _ in range(max(1, args.warmup)):
+            ixe.reset()
+            ixe.dedup(h_off, h_tok, out=h_flags)
+        barrier_sync()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ixe.reset()
+            ixe.dedup(h_off, h_tok, out=h_flags)
+        barrier_sync()
+        et = time.perf_counter() - t0
+        t = torch.tensor([et], device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        et = float(t.item())
+        ixe.close()
+        e2e = {"value": D * world * args.steps / et, "unit": "docs/s",
+               "h2d_bytes_per_step": (D + 1) * 8 + T * 4, "d2h_bytes_per_step": D}
+        del h_tok
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    cpu = None if args.skip_cpu else _cpu_baseline(spec, nexp, fp)
+    b = results["batched"]
+    line = {
+        "metric": "docs/s (LSHBloom dedup: shingle SHA-1, MinHash P=121, 11x11 bands, Bloom query+insert)",
+        "value": b["docs_per_s"], "unit": "docs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * b["seconds"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {D} docs, {T} tokens, {shingles} shingles",
+                   "P": P, "bands": BANDS, "rows": ROWS, "ngram": NGRAM, "n_expected": nexp,
+                   "fp_rate": fp, "l2": "inputs larger than L2 (tokens %.1f GB)" % (T * 4 / 1e9),
+                   "parallelism": f"replicas{world}"},
+        "shingle_hashes_per_s": b["shingle_hashes_per_s"],
+        "plain": ({"value": results["plain"]["docs_per_s"], "unit": "docs/s",
+                   "shingle_hashes_per_s": results["plain"]["shingle_hashes_per_s"]}
+                  if "plain" in results else None),
+        "dups_per_step": b["dups_per_step"],
+        "clocks": b["clocks"],
+        "e2e": e2e,
+        "gpu_launches": launches["batched"],
+        "roofline": {"bound": "alu", "kernel": "signature (SHA-1 + MinHash + band keys)",
+                     "achieved": achieved_imad / 1e12, "peak": peak_imad / 1e12,
+                     "unit": "T int-mul/s", "frac": achieved_imad / peak_imad, "traffic": None,
+                     "launch_ms": 1e3 * sb["sig_ms"] / 1e3 / max(1, sb["sig_chunks"]),
+                     "launches_per_step": sb["sig_chunks"] / args.steps,
+                     "perm_hashes_per_s": permhashes / sig_s,
+                     "peak_source": "152 SMs x 64 IMAD/clk x 2070 MHz (derived)"},
+        "stage_ms_per_step": {m: {"signature": v["sig_ms"] / args.steps,
+                                  "bloom": v["bloom_ms"] / args.steps} for m, v in stage.items()},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="pes2o_1m", choices=sorted(WORKLOADS))
+    ap.add_argument("--ref-docs", type=int, default=150)
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -111,6 +111,10 @@ typedef struct {
     double fill[64];          /* fraction of set bits per filter (first `bands`) */
     uint64_t resolve_rounds;  /* in-batch order-resolution iterations so far */
     uint64_t uncertain_docs;  /* documents that needed in-batch resolution */
+    uint64_t kernel_launches; /* kernels this library has launched in this process */
+    double sig_ms;            /* device time in the signature stage (CUDA events) */
+    double bloom_ms;          /* device time in the Bloom stage (CUDA events) */
+    uint64_t sig_chunks;      /* signature-stage launches timed in sig_ms */
 } lshb_stats;
 
 /* Fill *cfg with defaults: P=121, b=11, r=11, n=5, n_expected=10000,

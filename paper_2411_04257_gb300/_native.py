@@ -34,7 +34,8 @@ class Stats(C.Structure):
         ("exec_mode", C.c_uint32), ("item_shingles", C.c_uint32), ("m_bits", C.c_uint64),
         ("filter_bytes", C.c_uint64), ("docs_seen", C.c_uint64), ("dups_seen", C.c_uint64),
         ("fp_rate", C.c_double), ("fill", C.c_double * 64), ("resolve_rounds", C.c_uint64),
-        ("uncertain_docs", C.c_uint64),
+        ("uncertain_docs", C.c_uint64), ("kernel_launches", C.c_uint64),
+        ("sig_ms", C.c_double), ("bloom_ms", C.c_double), ("sig_chunks", C.c_uint64),
     ]
 
 

@@ -403,50 +403,50 @@ static int grid_for(uint64_t n, int threads) {
 
 cudaError_t launch_popcount(const uint32_t *words, uint64_t n, unsigned long long *out,
                             cudaStream_t s) {
-    k_popcount<<<grid_for(n, 256), 256, 0, s>>>(words, n, out);
+    k_popcount<<<grid_for(n, 256), 256, 0, s>>>(words, n, out); count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_probe_mark(const BloomArgs &a, cudaStream_t s) {
-    k_probe_mark<<<grid_for(a.D * a.bands, 256), 256, 0, s>>>(a);
+    k_probe_mark<<<grid_for(a.D * a.bands, 256), 256, 0, s>>>(a); count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_classify(const BloomArgs &a, uint32_t *block_counts, uint32_t *total,
                             uint32_t *ulist, cudaStream_t s) {
-    k_classify<<<grid_for(a.D * a.bands, 256), 256, 0, s>>>(a);
+    k_classify<<<grid_for(a.D * a.bands, 256), 256, 0, s>>>(a); count_launch();
     const uint32_t nb = (uint32_t)((a.D + 1023) / 1024);
-    k_status<<<nb, 1024, 0, s>>>(a, block_counts);
-    k_scan_counts<<<1, 1024, 0, s>>>(block_counts, nb, total);
-    k_compact<<<nb, 1024, 0, s>>>(a, block_counts, ulist);
+    k_status<<<nb, 1024, 0, s>>>(a, block_counts); count_launch();
+    k_scan_counts<<<1, 1024, 0, s>>>(block_counts, nb, total); count_launch();
+    k_compact<<<nb, 1024, 0, s>>>(a, block_counts, ulist); count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_count_keys(const BloomArgs &a, const uint32_t *ulist, uint32_t nu,
                               unsigned long long *count, cudaStream_t s) {
-    k_count_keys<<<grid_for((uint64_t)nu * a.bands, 256), 256, 0, s>>>(a, ulist, nu, count);
+    k_count_keys<<<grid_for((uint64_t)nu * a.bands, 256), 256, 0, s>>>(a, ulist, nu, count); count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_resolve_setup(const BloomArgs &a, const uint32_t *ulist, uint32_t nu,
                                  const ResolveTable &t, int insert_all, cudaStream_t s) {
-    k_rk_insert<<<grid_for((uint64_t)nu * a.bands, 256), 256, 0, s>>>(a, ulist, nu, t);
-    k_fixed_setters<<<grid_for(a.D * a.bands, 256), 256, 0, s>>>(a, t, insert_all);
-    k_cache_slots<<<grid_for((uint64_t)nu * a.bands, 128), 128, 0, s>>>(a, ulist, nu, t);
+    k_rk_insert<<<grid_for((uint64_t)nu * a.bands, 256), 256, 0, s>>>(a, ulist, nu, t); count_launch();
+    k_fixed_setters<<<grid_for(a.D * a.bands, 256), 256, 0, s>>>(a, t, insert_all); count_launch();
+    k_cache_slots<<<grid_for((uint64_t)nu * a.bands, 128), 128, 0, s>>>(a, ulist, nu, t); count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_resolve_iteration(const BloomArgs &a, const uint32_t *ulist, uint32_t nu,
                                      const ResolveTable &t, int insert_all, cudaStream_t s) {
-    k_iter_reset<<<grid_for((uint64_t)t.mask + 1, 256), 256, 0, s>>>(t);
-    if (!insert_all) k_iter_setters<<<grid_for((uint64_t)nu * a.bands, 256), 256, 0, s>>>(a, ulist, nu, t);
-    k_iter_eval<<<grid_for(nu, 256), 256, 0, s>>>(a, ulist, nu, t, insert_all);
+    k_iter_reset<<<grid_for((uint64_t)t.mask + 1, 256), 256, 0, s>>>(t); count_launch();
+    if (!insert_all) k_iter_setters<<<grid_for((uint64_t)nu * a.bands, 256), 256, 0, s>>>(a, ulist, nu, t); count_launch();
+    k_iter_eval<<<grid_for(nu, 256), 256, 0, s>>>(a, ulist, nu, t, insert_all); count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_resolve_sequential(const BloomArgs &a, const uint32_t *ulist, uint32_t nu,
                                       const ResolveTable &t, cudaStream_t s) {
-    k_sequential<<<1, 1, 0, s>>>(a, ulist, nu, t);
+    k_sequential<<<1, 1, 0, s>>>(a, ulist, nu, t); count_launch();
     return cudaGetLastError();
 }
 
@@ -454,8 +454,8 @@ cudaError_t launch_finalize_insert(const BloomArgs &a, const uint32_t *ulist, ui
                                    const ResolveTable &t, int insert_all, uint8_t *flags,
                                    uint8_t *insd, unsigned long long *dup_count, cudaStream_t s) {
     k_finalize<<<grid_for(a.D, 256), 256, 0, s>>>(a, ulist, nu, t, insert_all, flags, insd,
-                                                   dup_count);
-    k_insert<<<grid_for(a.D * a.bands, 256), 256, 0, s>>>(a, insd);
+                                                   dup_count); count_launch();
+    k_insert<<<grid_for(a.D * a.bands, 256), 256, 0, s>>>(a, insd); count_launch();
     return cudaGetLastError();
 }
 

@@ -37,6 +37,10 @@ struct SigArgs {
     PermSlice c;
 };
 
+// Process-wide count of kernels this library has launched.
+void count_launch(uint64_t n = 1);
+uint64_t launches_total();
+
 // Signature stage (sig_*.cu).
 int ngram_template(uint32_t ngram);  // 1, 5, or 0 (runtime n)
 cudaError_t launch_sig_fused_ng0(int pc, const SigArgs &a, cudaStream_t s);

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -42,6 +43,10 @@ lshb_status lshb::cuda_fail(cudaError_t e, const char *what) {
     } while (0)
 
 extern "C" const char *lshbloom_last_error(void) { return g_last_error.c_str(); }
+
+static std::atomic<uint64_t> g_launches{0};
+void lshb::count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+uint64_t lshb::launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 // ---- sizing and coefficients (host) ----------------------------------------------
 
@@ -97,6 +102,8 @@ lshbloom::~lshbloom() {
         if (ev_stage_free[i]) cudaEventDestroy(ev_stage_free[i]);
         if (ev_stage_ready[i]) cudaEventDestroy(ev_stage_ready[i]);
     }
+    for (int i = 0; i < 3; ++i)
+        if (ev_t[i]) cudaEventDestroy(ev_t[i]);
     if (counters) cudaFree(counters);
     if (host_counters) cudaFreeHost(host_counters);
     if (stream) cudaStreamDestroy(stream);
@@ -217,6 +224,7 @@ lshb_status lshb::init_handle(lshbloom *h, const lshb_config *cfg) {
         CK(cudaEventCreateWithFlags(&h->ev_stage_free[i], cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&h->ev_stage_ready[i], cudaEventDisableTiming));
     }
+    for (int i = 0; i < 3; ++i) CK(cudaEventCreate(&h->ev_t[i]));
     const size_t fbytes = (size_t)h->bands * h->words_per_filter * 4;
     cudaError_t e = cudaMalloc(&h->filters, fbytes);
     if (e != cudaSuccess) {
@@ -551,7 +559,20 @@ static lshb_status run_batch(lshbloom *h, const uint64_t *offsets, const uint32_
     if (job != Job::Hashes && !out_dev && (st = outbuf.reserve(Dc * out_row)) != LSHB_OK) return st;
 
     uint64_t *d_off_stage = (uint64_t *)h->buf(B_OFFSTAGE).ptr;
+    // Host tokens: chunk c+1 is copied on the copy stream into the other
+    // staging buffer while chunk c computes.
+    auto issue_copy = [&](size_t ci) -> lshb_status {
+        const int sb = (int)(ci & 1);
+        const uint64_t t0 = off[chunks[ci].first], nt = off[chunks[ci].second] - t0;
+        CK(cudaStreamWaitEvent(h->copy_stream, h->ev_stage_free[sb], 0));
+        if (nt) CK(cudaMemcpyAsync(h->stage_tok[sb].ptr, tokens + t0, nt * 4, cudaMemcpyHostToDevice,
+                                   h->copy_stream));
+        CK(cudaEventRecord(h->ev_stage_ready[sb], h->copy_stream));
+        return LSHB_OK;
+    };
+    if (!tok_dev && !chunks.empty() && (st = issue_copy(0)) != LSHB_OK) return st;
     for (size_t ci = 0; ci < chunks.size(); ++ci) {
+        if (!tok_dev && ci + 1 < chunks.size() && (st = issue_copy(ci + 1)) != LSHB_OK) return st;
         const uint64_t lo = chunks[ci].first, hi = chunks[ci].second, Dn = hi - lo;
         ChunkIn in;
         in.D = Dn;
@@ -566,19 +587,24 @@ static lshb_status run_batch(lshbloom *h, const uint64_t *offsets, const uint32_
             in.tok_base = off[lo];
         } else {
             const int sb = (int)(ci & 1);
-            const uint64_t t0 = off[lo], nt = off[hi] - off[lo];
-            CK(cudaStreamWaitEvent(h->copy_stream, h->ev_stage_free[sb], 0));
-            if (nt) CK(cudaMemcpyAsync(h->stage_tok[sb].ptr, tokens + t0, nt * 4,
-                                       cudaMemcpyHostToDevice, h->copy_stream));
-            CK(cudaEventRecord(h->ev_stage_ready[sb], h->copy_stream));
             CK(cudaStreamWaitEvent(s, h->ev_stage_ready[sb], 0));
             in.tokens = (const uint32_t *)h->stage_tok[sb].ptr;
-            in.tok_base = t0;
+            in.tok_base = off[lo];
         }
         if (job == Job::Dedup) {
+            CK(cudaEventRecord(h->ev_t[0], s));
             if ((st = run_signatures(h, in, nullptr, nullptr, true, s)) != LSHB_OK) return st;
+            CK(cudaEventRecord(h->ev_t[1], s));
             uint8_t *fl = out_dev ? (uint8_t *)out + lo : (uint8_t *)outbuf.ptr;
             if ((st = run_bloom(h, Dn, fl, s)) != LSHB_OK) return st;
+            CK(cudaEventRecord(h->ev_t[2], s));
+            CK(cudaEventSynchronize(h->ev_t[2]));
+            float ms_sig = 0.f, ms_bloom = 0.f;
+            CK(cudaEventElapsedTime(&ms_sig, h->ev_t[0], h->ev_t[1]));
+            CK(cudaEventElapsedTime(&ms_bloom, h->ev_t[1], h->ev_t[2]));
+            h->t_sig_ms += ms_sig;
+            h->t_bloom_ms += ms_bloom;
+            h->sig_chunks += 1;
             if (!out_dev) CK(cudaMemcpyAsync((uint8_t *)out + lo, fl, Dn, cudaMemcpyDeviceToHost, s));
             h->docs_seen += Dn;
         } else if (job == Job::Signatures) {
@@ -600,10 +626,6 @@ static lshb_status run_batch(lshbloom *h, const uint64_t *offsets, const uint32_
                 CK(cudaMemcpyAsync((uint32_t *)out + t0, ho, nt * 4, cudaMemcpyDeviceToHost, s));
         }
         if (!tok_dev) CK(cudaEventRecord(h->ev_stage_free[ci & 1], s));
-        if (!out_dev || !tok_dev) {
-            // host-visible results (and reuse of the staging buffers) need the chunk done
-            CK(cudaStreamSynchronize(s));
-        }
     }
     if (!require_device) CK(cudaStreamSynchronize(s));
     return LSHB_OK;
@@ -690,6 +712,10 @@ extern "C" lshb_status lshbloom_stats(lshbloom_t *h, lshb_stats *out) {
     out->fp_rate = h->p;
     out->resolve_rounds = h->resolve_rounds;
     out->uncertain_docs = h->uncertain_docs;
+    out->kernel_launches = launches_total();
+    out->sig_ms = h->t_sig_ms;
+    out->bloom_ms = h->t_bloom_ms;
+    out->sig_chunks = h->sig_chunks;
     unsigned long long *cnt = (unsigned long long *)(h->counters + C_POPCOUNT);
     for (uint32_t j = 0; j < h->bands; ++j) {
         CK(cudaMemsetAsync(cnt, 0, 8, h->stream));

@@ -81,6 +81,9 @@ struct lshbloom {
     bool batched_ready = false;
     lshb::BatchedState *batched = nullptr;
     uint64_t docs_seen = 0, dups_seen = 0, resolve_rounds = 0, uncertain_docs = 0;
+    cudaEvent_t ev_t[3] = {nullptr, nullptr, nullptr};  // stage timers
+    double t_sig_ms = 0.0, t_bloom_ms = 0.0;
+    uint64_t sig_chunks = 0;
 
     lshb::DevBuf &buf(lshb::BufId id) { return bufs[id]; }
     ~lshbloom();

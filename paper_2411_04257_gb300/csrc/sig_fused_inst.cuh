@@ -24,7 +24,7 @@ static cudaError_t LSHB_CAT(sig_go_ng, LSHB_NG)(const SigArgs &a, cudaStream_t s
     }
     const uint64_t need = (a.D + kSigThreads / 32 - 1) / (kSigThreads / 32);
     const int grid = (int)(need < (uint64_t)g ? (need > 0 ? need : 1) : (uint64_t)g);
-    k_sig_fused<LSHB_NG, PC><<<grid, kSigThreads, 0, s>>>(a);
+    k_sig_fused<LSHB_NG, PC><<<grid, kSigThreads, 0, s>>>(a); count_launch();
     return cudaGetLastError();
 }
 

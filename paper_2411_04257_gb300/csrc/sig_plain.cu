@@ -30,7 +30,7 @@ static cudaError_t hash_go(const SigArgs &a, cudaStream_t s) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (!g[dev & 63]) g[dev & 63] = occupancy_grid(k_shingle_hash<NG>, kSigThreads);
-    k_shingle_hash<NG><<<clamp_grid(g[dev & 63], a.D), kSigThreads, 0, s>>>(a);
+    k_shingle_hash<NG><<<clamp_grid(g[dev & 63], a.D), kSigThreads, 0, s>>>(a); count_launch();
     return cudaGetLastError();
 }
 
@@ -48,7 +48,7 @@ static cudaError_t minhash_go(const SigArgs &a, cudaStream_t s) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (!g[dev & 63]) g[dev & 63] = occupancy_grid(k_minhash_hashes<PC>, kSigThreads);
-    k_minhash_hashes<PC><<<clamp_grid(g[dev & 63], a.D), kSigThreads, 0, s>>>(a);
+    k_minhash_hashes<PC><<<clamp_grid(g[dev & 63], a.D), kSigThreads, 0, s>>>(a); count_launch();
     return cudaGetLastError();
 }
 
@@ -83,7 +83,7 @@ cudaError_t launch_band_keys(const uint32_t *sig, uint32_t P, uint32_t bands, ui
     uint64_t blocks = (n + 255) / 256;
     if (blocks == 0) blocks = 1;
     if (blocks > 65535ull * 16) blocks = 65535ull * 16;
-    k_band_keys<<<(unsigned)blocks, 256, 0, s>>>(sig, P, bands, rows, D, keys);
+    k_band_keys<<<(unsigned)blocks, 256, 0, s>>>(sig, P, bands, rows, D, keys); count_launch();
     return cudaGetLastError();
 }
 
