@@ -7,7 +7,7 @@
 
 namespace lshb {
 
-constexpr int kMaxPC = 128;       // permutations handled by one signature pass
+constexpr int kMaxPC = 256;       // permutations handled by one signature pass (8 per lane)
 constexpr int kSigThreads = 64;   // threads per signature block (2 warps)
 constexpr int kMaxBands = 64;
 constexpr int kMaxK = 64;
@@ -43,11 +43,11 @@ uint64_t launches_total();
 
 // Signature stage (sig_*.cu).
 int ngram_template(uint32_t ngram);  // 1, 5, or 0 (runtime n)
-cudaError_t launch_sig_fused_ng0(int pc, const SigArgs &a, cudaStream_t s);
-cudaError_t launch_sig_fused_ng1(int pc, const SigArgs &a, cudaStream_t s);
-cudaError_t launch_sig_fused_ng5(int pc, const SigArgs &a, cudaStream_t s);
+cudaError_t launch_sig_ng0(int ppl, const SigArgs &a, cudaStream_t s);
+cudaError_t launch_sig_ng1(int ppl, const SigArgs &a, cudaStream_t s);
+cudaError_t launch_sig_ng5(int ppl, const SigArgs &a, cudaStream_t s);
 cudaError_t launch_shingle_hash(int ngram_tmpl, const SigArgs &a, cudaStream_t s);
-cudaError_t launch_minhash_hashes(int pc, const SigArgs &a, cudaStream_t s);
+cudaError_t launch_minhash_hashes(int ppl, const SigArgs &a, cudaStream_t s);
 cudaError_t launch_band_keys(const uint32_t *sig, uint32_t P, uint32_t bands, uint32_t rows,
                              uint64_t D, uint64_t *keys, cudaStream_t s);
 

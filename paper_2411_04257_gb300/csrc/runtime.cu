@@ -155,21 +155,21 @@ static lshb_status validate_config(const lshb_config *c) {
     return LSHB_OK;
 }
 
-// Passes of the signature stage: the widest instantiated kernel, last pass the
-// narrowest one that covers what is left.
+// Passes of the signature stage: each pass covers up to 32*PPL permutations
+// (PPL in {1, 2, 4, 8} per lane); P <= 256 takes a single pass.
 static void plan_passes(lshbloom *h) {
     h->passes.clear();
     uint32_t p0 = 0;
     while (p0 < h->P) {
         const uint32_t rem = h->P - p0;
-        int pc = 128;
-        if (rem <= 32) pc = 32;
-        else if (rem <= 64) pc = 64;
-        else if (rem == 121) pc = 121;
-        const uint32_t npc = std::min<uint32_t>(rem, (uint32_t)pc);
+        int ppl = 8;
+        if (rem <= 32) ppl = 1;
+        else if (rem <= 64) ppl = 2;
+        else if (rem <= 128) ppl = 4;
+        const uint32_t npc = std::min<uint32_t>(rem, 32u * ppl);
         SigPass ps;
         ps.p0 = p0;
-        ps.pc = pc;
+        ps.ppl = ppl;
         ps.npc = npc;
         memset(&ps.c, 0, sizeof ps.c);
         for (uint32_t i = 0; i < npc; ++i) {
@@ -399,12 +399,12 @@ lshb_status lshb::run_signatures(lshbloom *h, const ChunkIn &in, uint32_t *sig_o
         a.keys_out = (single && want_keys && !plain) ? keys : nullptr;
         if (plain) {
             a.hashes = (const uint32_t *)h->buf(B_HASHES).ptr;
-            CK(launch_minhash_hashes(ps.pc, a, s));
+            CK(launch_minhash_hashes(ps.ppl, a, s));
         } else {
             cudaError_t e;
-            if (ngt == 5) e = launch_sig_fused_ng5(ps.pc, a, s);
-            else if (ngt == 1) e = launch_sig_fused_ng1(ps.pc, a, s);
-            else e = launch_sig_fused_ng0(ps.pc, a, s);
+            if (ngt == 5) e = launch_sig_ng5(ps.ppl, a, s);
+            else if (ngt == 1) e = launch_sig_ng1(ps.ppl, a, s);
+            else e = launch_sig_ng0(ps.ppl, a, s);
             CK(e);
         }
     }

@@ -41,7 +41,7 @@ enum CounterId {
 
 struct SigPass {
     uint32_t p0, npc;
-    int pc;
+    int ppl;  // permutations per lane of the kernel instantiation
     PermSlice c;
 };
 

@@ -1,11 +1,14 @@
 // Signature-stage kernels: warp-cooperative shingling, SHA-1 shingle hash,
-// MinHash minimum over a pass of PC permutations, band-key epilogue.
+// MinHash minimum over a pass of up to 32*PPL permutations, band-key epilogue.
 //
-// Layout: one warp per document (plain form).  Lane l hashes shingle s0+l of
-// each 32-shingle step and folds it into its own PC running minima; the
-// coefficients are constant-bank operands (the kernel parameter), so the hot
-// loop is IMAD.WIDE + ALU work on registers only.  At the end of a document
-// the 32 lanes' minima are reduced across the warp.
+// Layout: one warp per document (or per shingle range of one).  Each step the
+// 32 lanes hash 32 consecutive shingles (one SHA-1 each) into a per-warp
+// shared-memory slot; then every lane folds all 32 hashes, read back as
+// broadcast 128-bit loads, into the PPL permutations it owns: lane l owns
+// permutations l, l+32, ..., with their coefficients in registers.  The inner
+// loop is ~12 integer instructions per (shingle, permutation), the loop body
+// is small enough to stay in the instruction cache, and no cross-lane
+// reduction is needed at the end of a document.
 #pragma once
 
 #include "lshb_device.cuh"
@@ -13,31 +16,47 @@
 
 namespace lshb {
 
-template <int PC>
-struct SigOcc {
-    // Register cap: the PC minima stay live across the SHA-1 of the next step,
-    // which needs about 30 more; below these caps ptxas spills.
-    static constexpr int kMaxRegs = PC >= 96 ? 200 : 128;
+template <int PPL>
+struct LaneCoef {
+    uint32_t a0[PPL], a1[PPL];
+    uint64_t b0[PPL], b1[PPL];  // zero-extended: the 64-bit addends of the wide multiplies
+
+    __device__ __forceinline__ void load(const PermSlice &c, uint32_t npc, int lane) {
+#pragma unroll
+        for (int t = 0; t < PPL; ++t) {
+            const uint32_t i = lane + 32 * t;
+            const bool on = i < npc;
+            a0[t] = on ? c.a0[i] : 0u;
+            a1[t] = on ? c.a1[i] : 0u;
+            b0[t] = on ? c.b0[i] : 0u;
+            b1[t] = on ? c.b1[i] : 0u;
+        }
+    }
 };
 
-// Fold one shingle hash into the PC running minima.
-template <int PC>
-__device__ __forceinline__ void fold_perms(uint32_t (&mn)[PC], uint32_t h, const PermSlice &c) {
-#pragma unroll
-    for (int i = 0; i < PC; ++i) mn[i] = min(mn[i], perm_lo32(h, c.a0[i], c.a1[i], c.b0[i], c.b1[i]));
+// ((a*h + b) mod (2^61 - 1)) mod 2^32 with the addends already 64-bit.
+__device__ __forceinline__ uint32_t perm_lo32w(uint32_t h, uint32_t a0, uint32_t a1, uint64_t b0,
+                                               uint64_t b1) {
+    const uint64_t t = (uint64_t)a0 * h + b0;
+    const uint64_t V = (uint64_t)a1 * h + b1 + (t >> 32);
+    const uint64_t s1 = ((((V & 0x1fffffffull) << 32) | (uint32_t)t) + (V >> 29)) + 1ull;
+    return (uint32_t)s1 - 1u + (uint32_t)(s1 >> 61);
 }
 
-// Minimum across the warp, every lane ends with the full result.
-template <int PC>
-__device__ __forceinline__ void warp_min_all(uint32_t (&mn)[PC]) {
+template <int PPL>
+__device__ __forceinline__ void fold4(uint32_t (&mn)[PPL], const LaneCoef<PPL> &c, uint4 hv) {
 #pragma unroll
-    for (int i = 0; i < PC; ++i) {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) mn[i] = min(mn[i], __shfl_xor_sync(LSHB_FULL_MASK, mn[i], off));
+    for (int t = 0; t < PPL; ++t) {
+        uint32_t m = mn[t];
+        m = min(m, perm_lo32w(hv.x, c.a0[t], c.a1[t], c.b0[t], c.b1[t]));
+        m = min(m, perm_lo32w(hv.y, c.a0[t], c.a1[t], c.b0[t], c.b1[t]));
+        m = min(m, perm_lo32w(hv.z, c.a0[t], c.a1[t], c.b0[t], c.b1[t]));
+        m = min(m, perm_lo32w(hv.w, c.a0[t], c.a1[t], c.b0[t], c.b1[t]));
+        mn[t] = m;
     }
 }
 
-// Hash of shingle s0+lane of a document of L tokens (L >= n).  For NG > 0 the
+// Hash of shingle s0+lane of a document of L >= n tokens.  For NG > 0 the
 // window is assembled with shuffles from two coalesced loads; lanes past the
 // last shingle return an unspecified value.
 template <int NG>
@@ -66,59 +85,103 @@ __device__ __forceinline__ uint32_t window_hash(const uint32_t *tk, uint64_t L, 
     }
 }
 
-// Write the pass minima and (single full pass) the band keys.
-template <int PC>
-__device__ __forceinline__ void sig_epilogue(const SigArgs &A, uint64_t d, uint32_t (&mn)[PC],
-                                             uint32_t *smw, int lane) {
+// Number of shingles of a document of L tokens (a shorter-than-n document has
+// one shingle of all its tokens; an empty one has none).
+__device__ __forceinline__ uint64_t shingle_count(uint64_t L, uint32_t n) {
+    return L == 0 ? 0 : (L < n ? 1 : L - n + 1);
+}
+
+// Fold shingles [s_begin, s_end) of one document into the lane's minima.
+// hbuf is the warp's 32-entry, 16-byte aligned shared slot.  When `hashes` is
+// given the shingle hashes are read from it (plain form) instead of computed.
+template <int NG, int PPL>
+__device__ __forceinline__ void fold_range(uint32_t (&mn)[PPL], const LaneCoef<PPL> &cf,
+                                           const uint32_t *tk, uint64_t L, uint32_t n,
+                                           uint64_t s_begin, uint64_t s_end,
+                                           const uint32_t *hashes, uint32_t *hbuf, int lane) {
+    const uint64_t S = shingle_count(L, n);
+    if (L < n) {
+        // one short shingle of all L tokens (only when the range covers it)
+        if (s_begin == 0 && s_end > 0 && L > 0) {
+            uint32_t h = hashes ? __ldg(hashes) : bswap32(sha1_h0_tokens(tk, (uint32_t)L));
+            const uint4 hv = make_uint4(h, h, h, h);
+            fold4<PPL>(mn, cf, hv);
+        }
+        return;
+    }
+    for (uint64_t s0 = s_begin; s0 < s_end; s0 += 32) {
+        const uint32_t cnt = (uint32_t)min((uint64_t)32, s_end - s0);
+        uint32_t h;
+        if (hashes) {
+            h = (s0 + lane < s_end) ? __ldg(hashes + s0 + lane) : 0u;
+        } else {
+            h = window_hash<NG>(tk, L, S, s0, lane, n);
+        }
+        // lanes past the range repeat the first hash of the step: a repeat
+        // leaves every minimum unchanged.
+        const uint32_t h0 = __shfl_sync(LSHB_FULL_MASK, h, 0);
+        if ((uint32_t)lane >= cnt) h = h0;
+        __syncwarp();
+        hbuf[lane] = h;
+        __syncwarp();
+        const uint4 *hv4 = reinterpret_cast<const uint4 *>(hbuf);
+        const uint32_t groups = (cnt + 3) >> 2;
+        for (uint32_t g = 0; g < groups; ++g) fold4<PPL>(mn, cf, hv4[g]);
+    }
+}
+
+// Write the pass minima (sig_out) and, for a single full pass, band keys.
+template <int PPL>
+__device__ __forceinline__ void sig_epilogue(const SigArgs &A, uint64_t d, uint32_t (&mn)[PPL],
+                                             uint32_t *sigbuf, int lane) {
     if (A.sig_out) {
         uint32_t *row = A.sig_out + d * A.P + A.p0;
 #pragma unroll
-        for (int i = 0; i < PC; ++i)
-            if ((i & 31) == lane && i < (int)A.npc) row[i] = mn[i];
+        for (int t = 0; t < PPL; ++t)
+            if (lane + 32 * t < (int)A.npc) row[lane + 32 * t] = mn[t];
     }
     if (A.keys_out) {
+        __syncwarp();
 #pragma unroll
-        for (int i = 0; i < PC; ++i)
-            if ((i & 31) == lane) smw[i] = mn[i];
+        for (int t = 0; t < PPL; ++t) sigbuf[lane + 32 * t] = mn[t];
         __syncwarp();
         for (uint32_t j = lane; j < A.bands; j += 32) {
             uint64_t s = 0;
-            for (uint32_t t = 0; t < A.rows; ++t) s += smw[j * A.rows + t];
+            for (uint32_t t = 0; t < A.rows; ++t) s += sigbuf[j * A.rows + t];
             A.keys_out[d * A.bands + j] = s;
         }
         __syncwarp();
     }
 }
 
-template <int NG, int PC>
-__global__ void __maxnreg__(SigOcc<PC>::kMaxRegs)
-k_sig_fused(const __grid_constant__ SigArgs A) {
-    __shared__ uint32_t sm[kSigThreads / 32][PC];
+template <int PPL>
+struct SigSmem {
+    uint4 hbuf[kSigThreads / 32][8];          // 32 hashes per warp
+    uint32_t sig[kSigThreads / 32][32 * PPL];
+};
+
+// Fused signature kernel: shingling + SHA-1 + MinHash (+ band keys), warp per
+// document.  `hashes` in SigArgs switches it to the plain form's second stage.
+template <int NG, int PPL>
+__global__ void __launch_bounds__(kSigThreads) k_sig(const __grid_constant__ SigArgs A) {
+    __shared__ SigSmem<PPL> sm;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const uint64_t nwarps = (uint64_t)gridDim.x * (kSigThreads / 32);
     const uint32_t n = NG > 0 ? (uint32_t)NG : A.ngram;
+    LaneCoef<PPL> cf;
+    cf.load(A.c, A.npc, lane);
+    uint32_t *hbuf = reinterpret_cast<uint32_t *>(sm.hbuf[wib]);
     for (uint64_t d = (uint64_t)blockIdx.x * (kSigThreads / 32) + wib; d < A.D; d += nwarps) {
         const uint64_t o0 = A.offsets[d], o1 = A.offsets[d + 1];
         const uint64_t L = o1 - o0;
         const uint32_t *tk = A.tokens + (o0 - A.tok_base);
-        uint32_t mn[PC];
+        const uint32_t *hs = A.hashes ? A.hashes + (o0 - A.tok_base) : nullptr;
+        uint32_t mn[PPL];
 #pragma unroll
-        for (int i = 0; i < PC; ++i) mn[i] = 0xffffffffu;
-        if (L >= n) {
-            const uint64_t S = L - n + 1;
-            for (uint64_t s0 = 0; s0 < S; s0 += 32) {
-                uint32_t h = window_hash<NG>(tk, L, S, s0, lane, n);
-                const uint32_t h0 = __shfl_sync(LSHB_FULL_MASK, h, 0);
-                if (s0 + lane >= S) h = h0;  // a repeat of a real shingle leaves the minima unchanged
-                fold_perms<PC>(mn, h, A.c);
-            }
-        } else if (L > 0) {
-            const uint32_t h = bswap32(sha1_h0_tokens(tk, (uint32_t)L));
-            fold_perms<PC>(mn, h, A.c);
-        }
-        warp_min_all<PC>(mn);
-        sig_epilogue<PC>(A, d, mn, sm[wib], lane);
+        for (int t = 0; t < PPL; ++t) mn[t] = 0xffffffffu;
+        fold_range<NG, PPL>(mn, cf, tk, L, n, 0, shingle_count(L, n), hs, hbuf, lane);
+        sig_epilogue<PPL>(A, d, mn, sm.sig[wib], lane);
     }
 }
 
@@ -147,34 +210,6 @@ __global__ void __launch_bounds__(kSigThreads) k_shingle_hash(const __grid_const
             __syncwarp();
             if (lane == 0) out[0] = bswap32(sha1_h0_tokens(tk, (uint32_t)L));
         }
-    }
-}
-
-// Plain form, stage 2: MinHash minima over precomputed shingle hashes.
-template <int PC>
-__global__ void __maxnreg__(SigOcc<PC>::kMaxRegs)
-k_minhash_hashes(const __grid_constant__ SigArgs A) {
-    __shared__ uint32_t sm[kSigThreads / 32][PC];
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const uint64_t nwarps = (uint64_t)gridDim.x * (kSigThreads / 32);
-    for (uint64_t d = (uint64_t)blockIdx.x * (kSigThreads / 32) + wib; d < A.D; d += nwarps) {
-        const uint64_t o0 = A.offsets[d], o1 = A.offsets[d + 1];
-        const uint64_t L = o1 - o0;
-        const uint64_t S = L == 0 ? 0 : (L < A.ngram ? 1 : L - A.ngram + 1);
-        const uint32_t *hs = A.hashes + (o0 - A.tok_base);
-        uint32_t mn[PC];
-#pragma unroll
-        for (int i = 0; i < PC; ++i) mn[i] = 0xffffffffu;
-        if (S > 0) {
-            const uint32_t hfirst = __ldg(hs);
-            for (uint64_t s0 = 0; s0 < S; s0 += 32) {
-                const uint32_t h = (s0 + lane < S) ? __ldg(hs + s0 + lane) : hfirst;
-                fold_perms<PC>(mn, h, A.c);
-            }
-        }
-        warp_min_all<PC>(mn);
-        sig_epilogue<PC>(A, d, mn, sm[wib], lane);
     }
 }
 

@@ -1,5 +1,6 @@
-// Plain (one kernel per stage) signature path: shingle hashes to memory,
-// MinHash minima from them, band keys from the signature matrix.
+// Plain (one kernel per stage) signature path: shingle hashes to memory, then
+// MinHash minima from them (the signature kernel reading stored hashes), then
+// band keys from the signature matrix.
 #include "sig_kernels.cuh"
 
 namespace lshb {
@@ -42,24 +43,9 @@ cudaError_t launch_shingle_hash(int ngram_tmpl, const SigArgs &a, cudaStream_t s
     }
 }
 
-template <int PC>
-static cudaError_t minhash_go(const SigArgs &a, cudaStream_t s) {
-    static int g[64] = {0};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (!g[dev & 63]) g[dev & 63] = occupancy_grid(k_minhash_hashes<PC>, kSigThreads);
-    k_minhash_hashes<PC><<<clamp_grid(g[dev & 63], a.D), kSigThreads, 0, s>>>(a); count_launch();
-    return cudaGetLastError();
-}
-
-cudaError_t launch_minhash_hashes(int pc, const SigArgs &a, cudaStream_t s) {
-    switch (pc) {
-        case 32: return minhash_go<32>(a, s);
-        case 64: return minhash_go<64>(a, s);
-        case 121: return minhash_go<121>(a, s);
-        case 128: return minhash_go<128>(a, s);
-        default: return cudaErrorInvalidValue;
-    }
+// Stage 2 of the plain form: the generic signature kernel with `a.hashes` set.
+cudaError_t launch_minhash_hashes(int ppl, const SigArgs &a, cudaStream_t s) {
+    return launch_sig_ng0(ppl, a, s);
 }
 
 // Band key j of document d: sum of signature rows j*r .. j*r+r-1 (mod 2^64).
