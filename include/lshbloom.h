@@ -160,6 +160,29 @@ LSHB_API lshb_status lshbloom_signatures(lshbloom_t *h, const uint64_t *offsets,
 LSHB_API lshb_status lshbloom_band_keys(lshbloom_t *h, const uint64_t *offsets, const uint32_t *tokens,
                                uint64_t D, uint64_t *keys_out);
 
+/* Band keys like lshbloom_band_keys, for callers that cannot let the library
+ * allocate device memory (applications whose GPU memory all belongs to their
+ * own fixed-budget pool, or latency-critical loops where cudaMalloc's
+ * device-wide synchronisation would stall other streams).  The paper has no
+ * counterpart: this is a deployment variant of the same computation.
+ * The intermediate signature matrix lives in a 16 MiB array compiled into
+ * the library, which every GPU that loads the library holds until the
+ * process exits; D * P * 4 bytes must fit in it (D <= 34663 at P = 121),
+ * larger batches get LSHB_ERR_ARG with the limit in the message.
+ * offsets, tokens, keys_out: device pointers (as lshbloom_band_keys;
+ * keys_out is uint64[D][b]); work is ordered on `stream` (a cudaStream_t,
+ * NULL = legacy default stream) and the call waits for it once, after
+ * checking that the offsets do not decrease (LSHB_ERR_CSR otherwise).
+ * The first call on each device looks up the array's device address; make
+ * that first call before any stream capture.  All calls share the one array
+ * (each call rewrites every row it reads, nothing needs clearing): calls
+ * that overlap on the GPU, from two threads or two streams, race.
+ * A successful call allocates no memory; a failed one records its message
+ * for lshbloom_last_error. */
+LSHB_API lshb_status lshbloom_band_keys_static(lshbloom_t *h, const uint64_t *offsets,
+                                               const uint32_t *tokens, uint64_t D,
+                                               uint64_t *keys_out, void *stream);
+
 /* Shingle hashes (Sec. 4.1 base hash) of D documents: for document d,
  * h_out[offsets[d] - offsets[0] + s] is the hash of shingle s for
  * s < shingles(d); the other n-1 entries of each document are 0.

@@ -153,6 +153,21 @@ class LSHBloom:
         check(lib().lshbloom_band_keys(self._h, po, pt, D, pk))
         return keys
 
+    def band_keys_static(self, offsets, tokens, out=None, stream=None):
+        """Band keys through lshbloom_band_keys_static: no allocation inside
+        the library (device tensors only; `out` may be preallocated)."""
+        import torch
+        po, pt, D, like, keep = self._inputs(offsets, tokens)
+        if out is None:
+            pk, keys = _out(D, self.bands, np.uint64, "uint64", like)
+        else:
+            pk, keys, _ = _arg(out, np.uint64, ["uint64", "int64"])
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        check(lib().lshbloom_band_keys_static(self._h, po, pt, D, pk, C.c_void_p(sp)))
+        return keys
+
     def shingle_hashes(self, offsets, tokens):
         po, pt, D, like, keep = self._inputs(offsets, tokens)
         ko = keep[0]

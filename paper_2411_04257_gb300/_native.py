@@ -59,6 +59,7 @@ _SIGS = {
     "lshbloom_signatures": (C.c_int, [_VP, _VP, _VP, C.c_uint64, _VP]),
     "lshbloom_band_keys": (C.c_int, [_VP, _VP, _VP, C.c_uint64, _VP]),
     "lshbloom_shingle_hashes": (C.c_int, [_VP, _VP, _VP, C.c_uint64, _VP]),
+    "lshbloom_band_keys_static": (C.c_int, [_VP, _VP, _VP, C.c_uint64, _VP, _VP]),
     "lshbloom_coefficients": (C.c_int, [_VP, _VP, _VP]),
     "lshbloom_filter_bytes": (C.c_int, [_VP, C.c_uint32, _VP]),
     "lshbloom_reset": (C.c_int, [_VP]),
