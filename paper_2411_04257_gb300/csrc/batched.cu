@@ -1,22 +1,576 @@
 // Batched form of the path: one persistent fused kernel over a work queue of
 // (document, shingle range) items, launched through a captured CUDA graph.
+//
+// Per chunk the graph runs: per-document item counts, a scan, the item ->
+// document map, the persistent kernel (SHA-1 + MinHash for its item; a
+// document split over several items merges its minima with atomicMin and the
+// last item to finish forms the band keys and probes the filters), then the
+// classification of the Bloom stage.  The per-chunk pointers and sizes are
+// copied into a device-side parameter block at the start of the graph, so one
+// instantiated graph serves every chunk of a handle.  In-batch order
+// resolution and the insert follow on the host-driven path (they depend on how
+// many documents are uncertain).
+//
+// Long documents no longer serialise on one warp and heavy-tailed length
+// mixes balance across the GPU; the item size is picked by a short timing
+// sweep on the first chunk.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+
 #include "runtime_internal.h"
+#include "sig_kernels.cuh"
 
 namespace lshb {
 
-struct BatchedState {
-    int unused = 0;
+constexpr int kBatchThreads = 64;
+constexpr uint32_t kItemCandidates[] = {64, 128, 256, 512, 1024};
+
+struct DynParams {
+    const uint64_t *offsets;  // D+1
+    const uint32_t *tokens;   // document d at tokens[offsets[d] - tok_base]
+    uint64_t tok_base;
+    uint64_t D;
+    uint64_t n_items;         // written on the device by the scan
 };
 
-lshb_status run_batched(lshbloom *h, const uint64_t *, const uint32_t *, uint64_t, uint8_t *,
-                        const std::vector<uint64_t> &, bool, bool, bool, cudaStream_t) {
-    (void)h;
-    return fail(LSHB_ERR_ARG, "batched form not available");
+struct BatchArgs {
+    DynParams *dyn;
+    uint32_t item_shingles, ngram, P, npc, bands, rows, k, sketch_log2;
+    uint64_t m_bits, words_per_filter;
+    const uint32_t *filters;
+    uint32_t *item_count;      // D
+    uint64_t *item_start;      // D+1
+    uint64_t *block_sums;      // scan partials
+    uint32_t *item_doc;        // n_items
+    uint64_t item_cap;         // capacity of item_doc
+    uint32_t *pending;         // D: items of the document not finished yet
+    uint32_t *sig_partial;     // D x P: merged minima of split documents
+    unsigned long long *queue;
+    uint64_t *keys, *miss, *cand;
+    uint8_t *prehit;
+    uint32_t *sketch1, *sketch2;
+    uint32_t *error;
+    PermSlice c;
+};
+
+__device__ __forceinline__ uint64_t items_of(uint64_t L, uint32_t n, uint32_t item) {
+    const uint64_t S = shingle_count(L, n);
+    return S == 0 ? 1 : (S + item - 1) / item;
 }
+
+// Per document: item count, pending counter, cleared Bloom-stage flags and,
+// for a document split over several items, a signature row of 2^32-1.
+__global__ void k_batch_prepare(const __grid_constant__ BatchArgs A) {
+    const DynParams dp = *A.dyn;
+    for (uint64_t d = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; d < dp.D;
+         d += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t L = dp.offsets[d + 1] - dp.offsets[d];
+        const uint64_t it = items_of(L, A.ngram, A.item_shingles);
+        A.item_count[d] = (uint32_t)it;
+        A.pending[d] = (uint32_t)it;
+        A.cand[d] = 0;
+        A.prehit[d] = 0;
+        if (it > 1) {
+            uint32_t *row = A.sig_partial + d * A.P;
+            for (uint32_t p = 0; p < A.P; ++p) row[p] = 0xffffffffu;
+        }
+    }
+}
+
+// Exclusive scan of item counts into item_start (D+1 entries), three phases.
+constexpr int kScanBlock = 1024;
+
+__device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t *tot) {
+    __shared__ uint64_t warp_sums[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint64_t x = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint64_t y = __shfl_up_sync(LSHB_FULL_MASK, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) warp_sums[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint64_t s = warp_sums[lane];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint64_t y = __shfl_up_sync(LSHB_FULL_MASK, s, off);
+            if (lane >= off) s += y;
+        }
+        warp_sums[lane] = s;  // inclusive over warps
+    }
+    __syncthreads();
+    const uint64_t before = (w > 0 ? warp_sums[w - 1] : 0) + x - v;
+    if (tot) *tot = warp_sums[31];
+    __syncthreads();
+    return before;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_reduce(const __grid_constant__ BatchArgs A) {
+    const uint64_t D = A.dyn->D;
+    const uint64_t i = (uint64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    uint64_t tot = 0;
+    block_exclusive_scan(i < D ? A.item_count[i] : 0, &tot);
+    if (threadIdx.x == 0) A.block_sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_top(const __grid_constant__ BatchArgs A,
+                                                         uint32_t nb) {
+    __shared__ uint64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (uint32_t base = 0; base < nb; base += kScanBlock) {
+        const uint32_t i = base + threadIdx.x;
+        uint64_t tot = 0;
+        const uint64_t ex = block_exclusive_scan(i < nb ? A.block_sums[i] : 0, &tot);
+        if (i < nb) A.block_sums[i] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        A.dyn->n_items = carry;
+        if (carry > A.item_cap) atomicOr(A.error, kErrQueue);
+    }
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_down(const __grid_constant__ BatchArgs A) {
+    const uint64_t D = A.dyn->D;
+    const uint64_t i = (uint64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    const uint64_t ex = block_exclusive_scan(i < D ? A.item_count[i] : 0, nullptr);
+    if (i < D) A.item_start[i] = A.block_sums[blockIdx.x] + ex;
+    if (i == 0) A.item_start[D] = A.dyn->n_items;
+}
+
+__global__ void k_expand(const __grid_constant__ BatchArgs A) {
+    const uint64_t D = A.dyn->D;
+    const uint64_t cap = A.item_cap;
+    for (uint64_t d = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; d < D;
+         d += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t s = A.item_start[d], n = A.item_count[d];
+        for (uint64_t t = 0; t < n && s + t < cap; ++t) A.item_doc[s + t] = (uint32_t)d;
+    }
+}
+
+// The persistent kernel.  Every warp pops items until the queue is drained;
+// nothing waits on another warp, so the kernel cannot stall.
+template <int NG, int PPL>
+__global__ void __launch_bounds__(kBatchThreads) k_batched(const __grid_constant__ BatchArgs A) {
+    __shared__ SigSmem<PPL> sm;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const uint32_t n = NG > 0 ? (uint32_t)NG : A.ngram;
+    LaneCoef<PPL> cf;
+    cf.load(A.c, A.npc, lane);
+    uint32_t *hbuf = reinterpret_cast<uint32_t *>(sm.hbuf[wib]);
+    uint32_t *sigbuf = sm.sig[wib];
+    const DynParams dp = *A.dyn;
+    const uint64_t n_items = min(dp.n_items, A.item_cap);
+    for (;;) {
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(A.queue, 1ull);
+        it = __shfl_sync(LSHB_FULL_MASK, it, 0);
+        if (it >= n_items) break;
+        const uint64_t d = A.item_doc[it];
+        const uint64_t ibeg = A.item_start[d];
+        const uint64_t icnt = A.item_start[d + 1] - ibeg;
+        if (d >= dp.D || it < ibeg || it - ibeg >= icnt) {
+            if (lane == 0) atomicOr(A.error, kErrQueue);
+            continue;
+        }
+        const uint64_t o0 = dp.offsets[d];
+        const uint64_t L = dp.offsets[d + 1] - o0;
+        const uint32_t *tk = dp.tokens + (o0 - dp.tok_base);
+        const uint64_t S = shingle_count(L, n);
+        const uint64_t s_begin = (it - ibeg) * A.item_shingles;
+        const uint64_t s_end = min(S, s_begin + A.item_shingles);
+        uint32_t mn[PPL];
+#pragma unroll
+        for (int t = 0; t < PPL; ++t) mn[t] = 0xffffffffu;
+        fold_range<NG, PPL>(mn, cf, tk, L, n, s_begin, s_end, nullptr, hbuf, lane);
+        if (icnt > 1) {
+            uint32_t *row = A.sig_partial + d * A.P;
+#pragma unroll
+            for (int t = 0; t < PPL; ++t)
+                if (lane + 32 * t < (int)A.npc) atomicMin(row + lane + 32 * t, mn[t]);
+            __threadfence();
+            __syncwarp();
+            uint32_t last = 0;
+            if (lane == 0) last = atomicSub(A.pending + d, 1u) == 1u;
+            last = __shfl_sync(LSHB_FULL_MASK, last, 0);
+            if (!last) continue;
+            __threadfence();
+#pragma unroll
+            for (int t = 0; t < PPL; ++t)
+                if (lane + 32 * t < (int)A.npc) mn[t] = __ldcg(row + lane + 32 * t);
+        }
+        // band keys (Sec. 4.1) and the probes of this document (Sec. 4.2)
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < PPL; ++t) sigbuf[lane + 32 * t] = mn[t];
+        __syncwarp();
+        for (uint32_t j = lane; j < A.bands; j += 32) {
+            uint64_t key = 0;
+            for (uint32_t t = 0; t < A.rows; ++t) key += sigbuf[j * A.rows + t];
+            A.keys[d * A.bands + j] = key;
+            A.miss[d * A.bands + j] =
+                probe_band(A.filters + (uint64_t)j * A.words_per_filter, key, j, A.k, A.m_bits,
+                           A.sketch1, A.sketch2, A.sketch_log2);
+        }
+        __syncwarp();
+    }
+}
+
+// ---- host side ---------------------------------------------------------------------
+
+struct BatchedState {
+    uint64_t dcap = 0, item_cap = 0;
+    uint32_t item = 0;
+    int grid = 0;
+    DynParams *dyn = nullptr;         // device
+    DynParams *dyn_host = nullptr;    // pinned
+    DevBuf item_count, item_start, block_sums, item_doc, pending, sig_partial;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // bracket the persistent kernel
+    cudaStream_t cap_stream = nullptr;          // private stream for graph capture
+
+    void drop_graph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+    }
+    ~BatchedState() {
+        drop_graph();
+        item_count.release(); item_start.release(); block_sums.release();
+        item_doc.release(); pending.release(); sig_partial.release();
+        if (dyn) cudaFree(dyn);
+        if (dyn_host) cudaFreeHost(dyn_host);
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+    }
+};
 
 void destroy_batched_state(lshbloom *h) {
     delete h->batched;
     h->batched = nullptr;
+}
+
+#define BCK(call)                                                           \
+    do {                                                                    \
+        cudaError_t e_ = (call);                                            \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);                 \
+    } while (0)
+
+template <int NG, int PPL>
+static cudaError_t go_batched(const BatchArgs &a, int grid, cudaStream_t s) {
+    k_batched<NG, PPL><<<grid, kBatchThreads, 0, s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <int NG>
+static cudaError_t dispatch_ppl(int ppl, const BatchArgs &a, int grid, cudaStream_t s) {
+    switch (ppl) {
+        case 1: return go_batched<NG, 1>(a, grid, s);
+        case 2: return go_batched<NG, 2>(a, grid, s);
+        case 4: return go_batched<NG, 4>(a, grid, s);
+        case 8: return go_batched<NG, 8>(a, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+static cudaError_t launch_k_batched(int ngt, int ppl, const BatchArgs &a, int grid, cudaStream_t s) {
+    if (ngt == 5) return dispatch_ppl<5>(ppl, a, grid, s);
+    if (ngt == 1) return dispatch_ppl<1>(ppl, a, grid, s);
+    return dispatch_ppl<0>(ppl, a, grid, s);
+}
+
+template <int NG, int PPL>
+static int occ_batched() {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batched<NG, PPL>, kBatchThreads, 0);
+    return nb > 0 ? nb : 1;
+}
+
+static int batched_grid(int ngt, int ppl) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int nb = 1;
+#define LSHB_OCC(NGV)                                                    \
+    switch (ppl) {                                                        \
+        case 1: nb = occ_batched<NGV, 1>(); break;                        \
+        case 2: nb = occ_batched<NGV, 2>(); break;                        \
+        case 4: nb = occ_batched<NGV, 4>(); break;                        \
+        default: nb = occ_batched<NGV, 8>(); break;                       \
+    }
+    if (ngt == 5) { LSHB_OCC(5) } else if (ngt == 1) { LSHB_OCC(1) } else { LSHB_OCC(0) }
+#undef LSHB_OCC
+    return nb * (sms > 0 ? sms : 1);
+}
+
+static BatchArgs make_args(lshbloom *h, BatchedState *b) {
+    BatchArgs a;
+    memset(&a, 0, sizeof a);
+    const SigPass &ps = h->passes[0];
+    a.dyn = b->dyn;
+    a.item_shingles = b->item;
+    a.ngram = h->ngram;
+    a.P = h->P;
+    a.npc = ps.npc;
+    a.bands = h->bands;
+    a.rows = h->rows;
+    a.k = h->k;
+    a.m_bits = h->m;
+    a.words_per_filter = h->words_per_filter;
+    a.filters = h->filters;
+    a.item_count = (uint32_t *)b->item_count.ptr;
+    a.item_start = (uint64_t *)b->item_start.ptr;
+    a.block_sums = (uint64_t *)b->block_sums.ptr;
+    a.item_doc = (uint32_t *)b->item_doc.ptr;
+    a.item_cap = b->item_cap;
+    a.pending = (uint32_t *)b->pending.ptr;
+    a.sig_partial = (uint32_t *)b->sig_partial.ptr;
+    a.queue = (unsigned long long *)(h->counters + C_QUEUE);
+    a.keys = (uint64_t *)h->buf(B_KEYS).ptr;
+    a.miss = (uint64_t *)h->buf(B_MISS).ptr;
+    a.cand = (uint64_t *)h->buf(B_CAND).ptr;
+    a.prehit = (uint8_t *)h->buf(B_PREHIT).ptr;
+    a.sketch1 = (uint32_t *)h->buf(B_SKETCH1).ptr;
+    a.sketch2 = (uint32_t *)h->buf(B_SKETCH2).ptr;
+    a.error = h->counters + C_ERROR;
+    a.c = ps.c;
+    return a;
+}
+
+static uint32_t sketch_log2_for(lshbloom *h, uint64_t D) {
+    const uint64_t marks = std::max<uint64_t>(D * h->bands * h->k * 8, 1ull << 16);
+    uint32_t lg = 16;
+    while ((1ull << lg) < marks && lg < h->sketch_log2_cap) ++lg;
+    return lg;
+}
+
+// Everything before the host-side resolution, for the chunk described by the
+// device parameter block (enqueued on s; also what the graph captures).
+static lshb_status enqueue_front(lshbloom *h, BatchedState *b, BatchArgs a, bool with_bloom,
+                                 cudaStream_t s, bool time_kernel) {
+    const uint64_t dcap = b->dcap;
+    a.sketch_log2 = sketch_log2_for(h, dcap);
+    BCK(cudaMemcpyAsync(b->dyn, b->dyn_host, sizeof(DynParams), cudaMemcpyHostToDevice, s));
+    BCK(cudaMemsetAsync(h->counters, 0, 64, s));
+    const uint64_t sbytes = (1ull << a.sketch_log2) / 8;
+    BCK(cudaMemsetAsync(a.sketch1, 0, sbytes, s));
+    BCK(cudaMemsetAsync(a.sketch2, 0, sbytes, s));
+    const unsigned nb = (unsigned)((dcap + kScanBlock - 1) / kScanBlock);
+    unsigned pg = (unsigned)std::min<uint64_t>((dcap + 255) / 256, 16384);
+    k_batch_prepare<<<pg ? pg : 1, 256, 0, s>>>(a);
+    count_launch();
+    k_scan_reduce<<<nb ? nb : 1, kScanBlock, 0, s>>>(a);
+    count_launch();
+    k_scan_top<<<1, kScanBlock, 0, s>>>(a, nb ? nb : 1);
+    count_launch();
+    k_scan_down<<<nb ? nb : 1, kScanBlock, 0, s>>>(a);
+    count_launch();
+    k_expand<<<pg ? pg : 1, 256, 0, s>>>(a);
+    count_launch();
+    BCK(cudaGetLastError());
+    if (time_kernel) BCK(cudaEventRecord(b->ev0, s));
+    BCK(launch_k_batched(ngram_template(h->ngram), h->passes[0].ppl, a, b->grid, s));
+    if (time_kernel) BCK(cudaEventRecord(b->ev1, s));
+    if (with_bloom) {
+        BloomArgs A = bloom_args(h, dcap);
+        A.D_dev = &b->dyn->D;
+        A.sketch_bits_log2 = a.sketch_log2;
+        BCK(launch_classify(A, (uint32_t *)h->buf(B_BLOCKCNT).ptr, h->counters + C_NU,
+                            (uint32_t *)h->buf(B_ULIST).ptr, s));
+        BCK(cudaMemcpyAsync(h->host_counters, h->counters, 64, cudaMemcpyDeviceToHost, s));
+    }
+    return LSHB_OK;
+}
+
+static lshb_status ensure_state(lshbloom *h, uint64_t dcap, uint64_t tcap) {
+    BatchedState *b = h->batched;
+    if (!b) {
+        b = h->batched = new BatchedState();
+        BCK(cudaMalloc(&b->dyn, sizeof(DynParams)));
+        BCK(cudaMallocHost(&b->dyn_host, sizeof(DynParams)));
+        BCK(cudaEventCreate(&b->ev0));
+        BCK(cudaEventCreate(&b->ev1));
+        BCK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+    }
+    if (dcap > b->dcap) {
+        b->drop_graph();
+        b->dcap = dcap;
+    }
+    lshb_status st;
+    // item_doc capacity: every item but a document's last holds a full
+    // item of the smallest candidate size.
+    const uint64_t icap = tcap / kItemCandidates[0] + b->dcap + 1;
+    if (icap > b->item_cap) {
+        b->drop_graph();
+        b->item_cap = icap;
+    }
+    if ((st = b->item_count.reserve(b->dcap * 4)) != LSHB_OK) return st;
+    if ((st = b->item_start.reserve((b->dcap + 1) * 8)) != LSHB_OK) return st;
+    if ((st = b->block_sums.reserve(((b->dcap + kScanBlock - 1) / kScanBlock + 1) * 8)) != LSHB_OK)
+        return st;
+    if ((st = b->item_doc.reserve(b->item_cap * 4)) != LSHB_OK) return st;
+    if ((st = b->pending.reserve(b->dcap * 4)) != LSHB_OK) return st;
+    if ((st = b->sig_partial.reserve(b->dcap * h->P * 4)) != LSHB_OK) return st;
+    if ((st = ensure_chunk_scratch(h, b->dcap, 0, false, false)) != LSHB_OK) return st;
+    if (!b->grid) b->grid = batched_grid(ngram_template(h->ngram), h->passes[0].ppl);
+    return LSHB_OK;
+}
+
+// Time the persistent kernel alone for each item size on (a prefix of) the
+// first chunk and keep the fastest.
+static lshb_status autotune(lshbloom *h, const DynParams &chunk, cudaStream_t s) {
+    BatchedState *b = h->batched;
+    DynParams sample = chunk;
+    sample.D = std::min<uint64_t>(chunk.D, 1ull << 16);
+    float best = 1e30f;
+    uint32_t best_item = 256;
+    for (uint32_t item : kItemCandidates) {
+        b->item = item;
+        *b->dyn_host = sample;
+        lshb_status st = enqueue_front(h, b, make_args(h, b), false, s, true);
+        if (st != LSHB_OK) return st;
+        BCK(cudaStreamSynchronize(s));
+        float ms = 0.f;
+        BCK(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+        if (ms < best) {
+            best = ms;
+            best_item = item;
+        }
+    }
+    b->item = best_item;
+    h->item_shingles = best_item;
+    b->drop_graph();
+    return LSHB_OK;
+}
+
+static lshb_status ensure_graph(lshbloom *h, cudaStream_t s) {
+    BatchedState *b = h->batched;
+    if (b->exec) return LSHB_OK;
+    (void)s;
+    cudaStream_t cs = b->cap_stream;
+    const uint64_t counted = launches_total();
+    BCK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    lshb_status st = enqueue_front(h, b, make_args(h, b), true, cs, true);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    // capture enqueues nothing: take back what the launch wrappers counted
+    count_launch(counted - launches_total());
+    if (st != LSHB_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    b->graph = g;
+    BCK(cudaGraphInstantiate(&b->exec, g, 0));
+    return LSHB_OK;
+}
+
+lshb_status run_batched(lshbloom *h, const uint64_t *offsets, const uint32_t *tokens, uint64_t D,
+                        uint8_t *flags, const std::vector<uint64_t> &off, bool off_dev,
+                        bool tok_dev, bool out_dev, cudaStream_t s) {
+    // chunks: documents and (for staged or very large inputs) tokens bounded
+    const uint64_t dmax = h->max_docs_batched;
+    std::vector<std::pair<uint64_t, uint64_t>> chunks;
+    {
+        const uint64_t save_docs = h->max_docs, save_tok = h->max_tokens;
+        h->max_docs = dmax;
+        if (tok_dev) h->max_tokens = h->max_tokens_batched;
+        plan_chunks(h, off, true, chunks);
+        h->max_docs = save_docs;
+        h->max_tokens = save_tok;
+    }
+    uint64_t dcap = 0, tcap = 0;
+    for (auto &c : chunks) {
+        dcap = std::max(dcap, c.second - c.first);
+        tcap = std::max(tcap, off[c.second] - off[c.first]);
+    }
+    lshb_status st;
+    if ((st = ensure_state(h, dcap, tcap)) != LSHB_OK) return st;
+    if (!tok_dev && (st = ensure_stage(h, tcap)) != LSHB_OK) return st;
+    BatchedState *b = h->batched;
+    DevBuf &outbuf = h->buf(B_OUTSTAGE);
+    if (!out_dev && (st = outbuf.reserve(b->dcap)) != LSHB_OK) return st;
+    uint64_t *d_off_stage = (uint64_t *)h->buf(B_OFFSTAGE).ptr;
+
+    auto issue_copy = [&](size_t ci) -> lshb_status {
+        const int sb = (int)(ci & 1);
+        const uint64_t t0 = off[chunks[ci].first], nt = off[chunks[ci].second] - t0;
+        BCK(cudaStreamWaitEvent(h->copy_stream, h->ev_stage_free[sb], 0));
+        if (nt) BCK(cudaMemcpyAsync(h->stage_tok[sb].ptr, tokens + t0, nt * 4, cudaMemcpyHostToDevice,
+                                    h->copy_stream));
+        BCK(cudaEventRecord(h->ev_stage_ready[sb], h->copy_stream));
+        return LSHB_OK;
+    };
+
+    for (size_t ci = 0; ci < chunks.size(); ++ci) {
+        const uint64_t lo = chunks[ci].first, hi = chunks[ci].second, Dn = hi - lo;
+        DynParams dp;
+        dp.D = Dn;
+        dp.n_items = 0;
+        if (off_dev) {
+            dp.offsets = offsets + lo;
+        } else {
+            BCK(cudaMemcpyAsync(d_off_stage, offsets + lo, (Dn + 1) * 8, cudaMemcpyHostToDevice, s));
+            dp.offsets = d_off_stage;
+        }
+        if (tok_dev) {
+            dp.tokens = tokens + off[lo];
+            dp.tok_base = off[lo];
+        } else {
+            if (ci == 0 && (st = issue_copy(0)) != LSHB_OK) return st;
+            if (ci + 1 < chunks.size() && (st = issue_copy(ci + 1)) != LSHB_OK) return st;
+            BCK(cudaStreamWaitEvent(s, h->ev_stage_ready[ci & 1], 0));
+            dp.tokens = (const uint32_t *)h->stage_tok[ci & 1].ptr;
+            dp.tok_base = off[lo];
+        }
+        if (b->item == 0) {
+            if (h->cfg.item_shingles) {
+                b->item = h->cfg.item_shingles;
+                h->item_shingles = b->item;
+            } else {
+                BCK(cudaStreamSynchronize(s));
+                if ((st = autotune(h, dp, s)) != LSHB_OK) return st;
+            }
+        }
+        if ((st = ensure_graph(h, s)) != LSHB_OK) return st;
+        BCK(cudaStreamSynchronize(s));  // the parameter block is read by the graph
+        *b->dyn_host = dp;
+        BCK(cudaEventRecord(h->ev_t[0], s));
+        BCK(cudaGraphLaunch(b->exec, s));
+        count_launch(10);  // prepare, 3 scan, expand, persistent, 4 classify kernels
+        BCK(cudaEventRecord(h->ev_t[1], s));
+        BCK(cudaStreamSynchronize(s));
+        float ms_k7 = 0.f;
+        BCK(cudaEventElapsedTime(&ms_k7, b->ev0, b->ev1));
+        BloomArgs A = bloom_args(h, Dn);
+        A.sketch_bits_log2 = sketch_log2_for(h, b->dcap);
+        uint8_t *fl = out_dev ? flags + lo : (uint8_t *)outbuf.ptr;
+        if ((st = resolve_and_insert(h, A, fl, s)) != LSHB_OK) return st;
+        BCK(cudaEventRecord(h->ev_t[2], s));
+        if (!out_dev) BCK(cudaMemcpyAsync(flags + lo, fl, Dn, cudaMemcpyDeviceToHost, s));
+        if (!tok_dev) BCK(cudaEventRecord(h->ev_stage_free[ci & 1], s));
+        BCK(cudaEventSynchronize(h->ev_t[2]));
+        float ms_all = 0.f;
+        BCK(cudaEventElapsedTime(&ms_all, h->ev_t[0], h->ev_t[2]));
+        h->t_sig_ms += ms_k7;                  // the persistent kernel
+        h->t_bloom_ms += ms_all - ms_k7;       // everything else of the chunk
+        h->sig_chunks += 1;
+        h->docs_seen += Dn;
+    }
+    BCK(cudaStreamSynchronize(s));
+    return LSHB_OK;
 }
 
 }  // namespace lshb

@@ -27,47 +27,22 @@
 
 namespace lshb {
 
-__device__ __forceinline__ uint64_t sketch_index(uint64_t g, uint32_t log2n) {
-    return (g * kGolden) >> (64 - log2n);
-}
-
 __global__ void k_probe_mark(const __grid_constant__ BloomArgs A) {
     const uint64_t n = A.D * A.bands;
     for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
          idx += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t j = (uint32_t)(idx % A.bands);
-        const ProbeSeq ps(A.keys[idx], j);
-        const uint32_t *F = A.filters + (uint64_t)j * A.words_per_filter;
-        uint64_t miss = 0;
-        for (uint32_t u0 = 0; u0 < A.k; u0 += 8) {
-            uint64_t q[8];
-            uint32_t w[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                q[i] = ps.pos(u0 + i, A.m_bits);
-                w[i] = (u0 + i < A.k) ? __ldg(F + (q[i] >> 5)) : 0xffffffffu;
-            }
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-                if (!((w[i] >> (q[i] & 31)) & 1u)) miss |= 1ull << (u0 + i);
-        }
-        A.miss[idx] = miss;
-        if (A.sketch1 == nullptr) continue;
-        uint64_t mm = miss;
-        while (mm) {
-            const uint32_t u = __ffsll((long long)mm) - 1;
-            mm &= mm - 1;
-            const uint64_t g = (uint64_t)j * A.m_bits + ps.pos(u, A.m_bits);
-            const uint64_t si = sketch_index(g, A.sketch_bits_log2);
-            const uint32_t bit = 1u << (si & 31);
-            const uint32_t old = atomicOr(A.sketch1 + (si >> 5), bit);
-            if (old & bit) atomicOr(A.sketch2 + (si >> 5), bit);
-        }
+        A.miss[idx] = probe_band(A.filters + (uint64_t)j * A.words_per_filter, A.keys[idx], j, A.k,
+                                 A.m_bits, A.sketch1, A.sketch2, A.sketch_bits_log2);
     }
 }
 
+__device__ __forceinline__ uint64_t batch_docs(const BloomArgs &A) {
+    return A.D_dev ? *A.D_dev : A.D;
+}
+
 __global__ void k_classify(const __grid_constant__ BloomArgs A) {
-    const uint64_t n = A.D * A.bands;
+    const uint64_t n = batch_docs(A) * A.bands;
     for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
          idx += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t d = idx / A.bands;
@@ -98,7 +73,7 @@ __global__ void __launch_bounds__(1024) k_status(const __grid_constant__ BloomAr
     __shared__ uint32_t warp_cnt[32];
     const uint64_t d = (uint64_t)blockIdx.x * 1024 + threadIdx.x;
     uint8_t st = 0;
-    if (d < A.D) {
+    if (d < batch_docs(A)) {
         st = A.prehit[d] ? 1 : (A.cand[d] ? 2 : 0);
         A.status[d] = st;
     }
@@ -144,7 +119,7 @@ __global__ void __launch_bounds__(1024) k_compact(const __grid_constant__ BloomA
                                                   const uint32_t *block_offsets, uint32_t *ulist) {
     __shared__ uint32_t warp_pre[32];
     const uint64_t d = (uint64_t)blockIdx.x * 1024 + threadIdx.x;
-    const bool u = d < A.D && A.status[d] == 2;
+    const bool u = d < batch_docs(A) && A.status[d] == 2;
     const uint32_t bal = __ballot_sync(LSHB_FULL_MASK, u);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0) warp_pre[w] = __popc(bal);

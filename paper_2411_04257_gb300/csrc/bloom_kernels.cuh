@@ -11,6 +11,7 @@ constexpr uint32_t kErrQueue = 2u;       // persistent kernel work-queue inconsi
 
 struct BloomArgs {
     uint64_t D;
+    const uint64_t *D_dev;      // when set, the batch size is read from device memory
     uint32_t bands, k;
     uint64_t m_bits, words_per_filter;
     uint32_t *filters;          // bands x words_per_filter
@@ -34,6 +35,42 @@ struct ResolveTable {
     uint8_t *udup;              // nu: duplicate in the current sweep
     uint32_t *changed;
 };
+
+__device__ __forceinline__ uint64_t sketch_index(uint64_t g, uint32_t log2n) {
+    return (g * kGolden) >> (64 - log2n);
+}
+
+// Probe one band key against its filter F (pre-batch bits): returns the mask
+// of probes that found a clear bit, and marks each such bit in the two-level
+// sketch (first mark sets sketch1, any later mark sets sketch2).
+__device__ __forceinline__ uint64_t probe_band(const uint32_t *F, uint64_t key, uint32_t j,
+                                               uint32_t k, uint64_t m, uint32_t *sk1, uint32_t *sk2,
+                                               uint32_t sk_log2) {
+    const ProbeSeq ps(key, j);
+    uint64_t miss = 0;
+    for (uint32_t u0 = 0; u0 < k; u0 += 8) {
+        uint64_t q[8];
+        uint32_t w[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            q[i] = ps.pos(u0 + i, m);
+            w[i] = (u0 + i < k) ? __ldg(F + (q[i] >> 5)) : 0xffffffffu;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (!((w[i] >> (q[i] & 31)) & 1u)) miss |= 1ull << (u0 + i);
+    }
+    uint64_t mm = miss;
+    while (mm) {
+        const uint32_t u = __ffsll((long long)mm) - 1;
+        mm &= mm - 1;
+        const uint64_t si = sketch_index((uint64_t)j * m + ps.pos(u, m), sk_log2);
+        const uint32_t bit = 1u << (si & 31);
+        const uint32_t old = atomicOr(sk1 + (si >> 5), bit);
+        if (old & bit) atomicOr(sk2 + (si >> 5), bit);
+    }
+    return miss;
+}
 
 cudaError_t launch_probe_mark(const BloomArgs &a, cudaStream_t s);
 cudaError_t launch_classify(const BloomArgs &a, uint32_t *block_counts, uint32_t *total,

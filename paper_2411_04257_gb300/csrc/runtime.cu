@@ -143,6 +143,8 @@ static lshb_status validate_config(const lshb_config *c) {
     if (!(c->fp_rate > 0.0 && c->fp_rate < 1.0)) return fail(LSHB_ERR_ARG, "fp_rate must be in (0,1)");
     if (c->insert_mode > 1) return fail(LSHB_ERR_ARG, "bad insert_mode");
     if (c->exec_mode > 1) return fail(LSHB_ERR_ARG, "bad exec_mode");
+    if (c->item_shingles != 0 && (c->item_shingles < 64 || c->item_shingles > (1u << 20)))
+        return fail(LSHB_ERR_ARG, "item_shingles must be 0 (autotuned) or 64..2^20");
     if ((c->perm_a == nullptr) != (c->perm_b == nullptr))
         return fail(LSHB_ERR_ARG, "perm_a and perm_b must be given together");
     if (c->perm_a) {
@@ -213,6 +215,9 @@ lshb_status lshb::init_handle(lshbloom *h, const lshb_config *cfg) {
     h->max_docs = cfg->max_batch_docs ? cfg->max_batch_docs : (1ull << 18);
     h->max_docs = std::min<uint64_t>(h->max_docs, 1ull << 22);
     h->max_tokens = cfg->max_batch_tokens ? cfg->max_batch_tokens : (1ull << 28);
+    // The batched form keeps no per-token scratch: larger chunks, fewer tails.
+    h->max_docs_batched = cfg->max_batch_docs ? h->max_docs : (1ull << 20);
+    h->max_tokens_batched = cfg->max_batch_tokens ? h->max_tokens : (1ull << 31);
 
     int dev = cfg->device;
     if (dev < 0) CK(cudaGetDevice(&dev));
@@ -452,6 +457,15 @@ lshb_status lshb::run_bloom(lshbloom *h, uint64_t D, uint8_t *flags_dev, cudaStr
     CK(launch_classify(A, (uint32_t *)h->buf(B_BLOCKCNT).ptr, h->counters + C_NU, ulist, s));
     CK(cudaMemcpyAsync(h->host_counters, h->counters, 64, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    return resolve_and_insert(h, A, flags_dev, s);
+}
+
+// Second half of the Bloom stage, once probes and the classification are in
+// place and the counters have been read back: resolve the uncertain
+// documents in stream order, write the flags, insert.
+lshb_status lshb::resolve_and_insert(lshbloom *h, const BloomArgs &A, uint8_t *flags_dev,
+                                     cudaStream_t s) {
+    uint32_t *ulist = (uint32_t *)h->buf(B_ULIST).ptr;
     const uint32_t nu = h->host_counters[C_NU];
     ResolveTable T;
     memset(&T, 0, sizeof T);
@@ -534,7 +548,7 @@ static lshb_status run_batch(lshbloom *h, const uint64_t *offsets, const uint32_
     std::vector<uint64_t> off;
     lshb_status st = host_offsets(h, offsets, D, off_dev, off);
     if (st != LSHB_OK) return st;
-    if (job == Job::Dedup && h->cfg.exec_mode == LSHB_EXEC_BATCHED && h->batched_ready) {
+    if (job == Job::Dedup && h->cfg.exec_mode == LSHB_EXEC_BATCHED && h->passes.size() == 1) {
         return run_batched(h, offsets, tokens, D, (uint8_t *)out, off, off_dev, tok_dev, out_dev, s);
     }
     const bool plain = h->cfg.exec_mode == LSHB_EXEC_PLAIN;

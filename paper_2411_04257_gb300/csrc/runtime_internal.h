@@ -76,9 +76,9 @@ struct lshbloom {
     uint32_t *host_counters = nullptr;  // pinned mirror
     lshb::DevBuf bufs[lshb::B_NBUF];
     uint64_t max_docs = 0, max_tokens = 0;
+    uint64_t max_docs_batched = 0, max_tokens_batched = 0;
     uint32_t sketch_log2_cap = 0;
     uint32_t item_shingles = 0;
-    bool batched_ready = false;
     lshb::BatchedState *batched = nullptr;
     uint64_t docs_seen = 0, dups_seen = 0, resolve_rounds = 0, uncertain_docs = 0;
     cudaEvent_t ev_t[3] = {nullptr, nullptr, nullptr};  // stage timers
@@ -106,6 +106,8 @@ lshb_status run_signatures(lshbloom *h, const ChunkIn &in, uint32_t *sig_out, ui
                            bool want_keys, cudaStream_t s);
 BloomArgs bloom_args(lshbloom *h, uint64_t D);
 lshb_status run_bloom(lshbloom *h, uint64_t D, uint8_t *flags_dev, cudaStream_t s);
+lshb_status resolve_and_insert(lshbloom *h, const BloomArgs &A, uint8_t *flags_dev,
+                               cudaStream_t s);
 
 // Batched (persistent, graph-launched) form.
 lshb_status run_batched(lshbloom *h, const uint64_t *offsets, const uint32_t *tokens, uint64_t D,

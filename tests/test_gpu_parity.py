@@ -122,6 +122,22 @@ def test_dedup_plain_10k_workload(lshb, oracle, corpus, exec_mode, insert_all):
     assert want.sum() >= 10
 
 
+@pytest.mark.parametrize("item", [64, 1024, 0])
+def test_batched_split_documents_heavy_tail(lshb, oracle, corpus, item):
+    """Pareto(1.2) lengths up to 40,000 tokens: with 64-shingle items the long
+    documents are split over hundreds of warps and merged by atomicMin; 0
+    lets the autotuner pick."""
+    spec = corpus.CorpusSpec(n_docs=2500, seed=13, vocab=20_000, length_law="pareto",
+                             pareto_alpha=1.2, length_min=20, length_max=40_000, dup_frac=0.3,
+                             dup_lo=0.0, dup_hi=0.05)
+    off, tok = corpus.generate(spec)
+    want, st = _check_dedup(lshb, oracle, off, tok, exec_mode="batched", item_shingles=item)
+    assert want.sum() > 100
+    assert st["item_shingles"] in (64, 128, 256, 512, 1024)
+    if item:
+        assert st["item_shingles"] == item
+
+
 def test_dedup_many_calls_and_small_chunks(lshb, oracle, corpus):
     off, tok = _small_corpus(corpus, n=1500, dup_frac=0.5)
     _check_dedup(lshb, oracle, off, tok, calls=[0, 1, 2, 100, 101, 700, 1500],
