@@ -380,9 +380,14 @@ static lshb_status enqueue_front(lshbloom *h, BatchedState *b, BatchArgs a, bool
     k_expand<<<pg ? pg : 1, 256, 0, s>>>(a);
     count_launch();
     BCK(cudaGetLastError());
-    if (time_kernel) BCK(cudaEventRecord(b->ev0, s));
+    // Under capture the records must be external to become event-record nodes
+    // of the graph (then every replay times the persistent kernel).
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    BCK(cudaStreamIsCapturing(s, &cap));
+    const unsigned rec_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
+    if (time_kernel) BCK(cudaEventRecordWithFlags(b->ev0, s, rec_flags));
     BCK(launch_k_batched(ngram_template(h->ngram), h->passes[0].ppl, a, b->grid, s));
-    if (time_kernel) BCK(cudaEventRecord(b->ev1, s));
+    if (time_kernel) BCK(cudaEventRecordWithFlags(b->ev1, s, rec_flags));
     if (with_bloom) {
         BloomArgs A = bloom_args(h, dcap);
         A.D_dev = &b->dyn->D;
