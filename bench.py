@@ -151,6 +151,81 @@ def run_reference(args):
     return 0
 
 
+def _serve_bench(local, seconds_per_load=3.0, n_docs=200_000, seed=0):
+    """Continuous-batching server over 4 resident indexes (n = 100M each):
+    requests of 1-4,096 documents (log-uniform) cut cyclically from a
+    serving-shaped corpus (lognormal median 1,000 tokens, 10% near-dups).
+    A burst gives the saturation rate; Poisson arrivals at 25/60/90% of it
+    give latency percentiles."""
+    import dataclasses
+
+    import numpy as np
+    import torch
+
+    from paper_2411_04257_gb300 import LSHBloom, LSHBloomServer
+    from synth import corpus
+    from synth import gpu as sgpu
+
+    spec = dataclasses.replace(corpus.serving_requests(seed=seed), n_docs=n_docs)
+    off_d, tok_d = sgpu.DeviceCorpus(spec, torch.device("cuda", local)).generate(0, n_docs)
+    off_h = off_d.cpu().numpy().view(np.uint64)
+    tok_h = tok_d.cpu().numpy().view(np.uint32)
+    del off_d, tok_d
+    rnd = np.random.default_rng(seed)
+    cursor = [0]
+
+    def next_request():
+        D = int(np.exp(rnd.uniform(0.0, np.log(4096.0))))
+        D = max(1, min(D, 4096))
+        lo = cursor[0] if cursor[0] + D <= n_docs else 0
+        cursor[0] = lo + D
+        return int(rnd.integers(0, 4)), off_h[lo:lo + D + 1], D
+
+    ixs = [LSHBloom(P, BANDS, ROWS, n_expected=100_000_000, fp_rate=1e-5, ngram=NGRAM,
+                    device=local) for _ in range(4)]
+    srv = LSHBloomServer(ixs, mem_budget_bytes=4 << 30, max_inflight=64)
+
+    def run(reqs, arrivals):
+        t0 = time.perf_counter()
+        tickets = []
+        for (i, o, D), at in zip(reqs, arrivals):
+            while True:
+                now = time.perf_counter() - t0
+                if now >= at:
+                    break
+                if at - now > 2e-4:
+                    time.sleep((at - now) / 2)
+            tickets.append((srv.submit(i, o, tok_h), D))
+        lats, docs = [], 0
+        for t, D in tickets:
+            _, lat = srv.wait(t)
+            lats.append(lat)
+            docs += D
+        span = time.perf_counter() - t0
+        return docs / span, np.percentile(lats, 50) / 1e3, np.percentile(lats, 99) / 1e3, len(lats)
+
+    warm = [next_request() for _ in range(64)]
+    run(warm, [0.0] * len(warm))
+    burst = [next_request() for _ in range(600)]
+    sat, p50, p99, n = run(burst, [0.0] * len(burst))
+    out = {"indexes": 4, "n_expected_per_index": 100_000_000, "max_inflight": 64,
+           "mem_budget_gb": 4, "saturation_docs_per_s": sat,
+           "burst": {"requests": n, "p50_ms": p50, "p99_ms": p99}, "loads": []}
+    mean_docs = 4095.0 / np.log(4096.0)
+    for frac in (0.25, 0.60, 0.90):
+        rate_req = frac * sat / mean_docs
+        n_req = max(50, int(rate_req * seconds_per_load))
+        reqs = [next_request() for _ in range(n_req)]
+        arrivals = np.cumsum(rnd.exponential(1.0 / rate_req, n_req))
+        v, p50, p99, n = run(reqs, arrivals)
+        out["loads"].append({"offered_frac": frac, "offered_docs_per_s": frac * sat,
+                             "docs_per_s": v, "p50_ms": p50, "p99_ms": p99, "requests": n})
+    srv.close()
+    for ix in ixs:
+        ix.close()
+    return out
+
+
 def _time_steps(fn, steps, warmup, stream, sync, on_start=None):
     import torch
     for _ in range(warmup):
@@ -201,6 +276,7 @@ def run_ours(args):
     results = {}
     launches = {}
     stage = {}
+    item_shingles = None
     for mode in (["batched", "plain"] if not args.skip_plain else ["batched"]):
         ix = LSHBloom(P, BANDS, ROWS, n_expected=nexp, fp_rate=fp, ngram=NGRAM, exec_mode=mode,
                       device=local)
@@ -216,6 +292,8 @@ def run_ours(args):
                              on_start=lambda: s0.update(ix.stats()))
         clocks = ck.summary()
         s1 = ix.stats()
+        if mode == "batched":
+            item_shingles = s1["item_shingles"]
         launches[mode] = s1["kernel_launches"] - s0["kernel_launches"]
         stage[mode] = {"sig_ms": s1["sig_ms"] - s0["sig_ms"],
                        "bloom_ms": s1["bloom_ms"] - s0["bloom_ms"],
@@ -268,6 +346,12 @@ def run_ours(args):
                "h2d_bytes_per_step": (D + 1) * 8 + T * 4, "d2h_bytes_per_step": D}
         del h_tok
 
+    serve = None
+    if not args.skip_serve:
+        del off, tok
+        torch.cuda.empty_cache()
+        serve = _serve_bench(local)
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -301,6 +385,8 @@ def run_ours(args):
                      "peak_source": "152 SMs x 64 IMAD/clk x 2070 MHz (derived)"},
         "stage_ms_per_step": {m: {"signature": v["sig_ms"] / args.steps,
                                   "bloom": v["bloom_ms"] / args.steps} for m, v in stage.items()},
+        "serve": serve,
+        "item_shingles": item_shingles,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
@@ -320,6 +406,7 @@ def main():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-serve", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -213,6 +213,47 @@ LSHB_API lshb_status lshbloom_load(const char *path, int32_t device, lshbloom_t 
  * positive and false negative integrals at threshold T (Eqs. 1-2, Sec. 4.3). */
 LSHB_API lshb_status lshbloom_optimal_br(double T, uint32_t P, uint32_t *b_out, uint32_t *r_out);
 
+/* ---- Serving: continuous batching over resident indexes ----------------------
+ *
+ * A server owns a device-memory budget and a worker thread.  Requests (CSR
+ * batches for one of its indexes) are admitted in arrival order as soon as an
+ * in-flight slot and enough of the budget are free; the copy-in and the
+ * signature stage of every admitted request run at once on separate streams,
+ * so requests that arrive while others are on the GPU join them there.  The
+ * Bloom stage of each index runs in arrival order, so every request is judged
+ * against exactly the documents submitted before it to the same index
+ * (Sec. 2.1): its flags equal those of lshbloom_dedup calls made one after
+ * the other in submission order.  The filters stay resident across requests. */
+typedef struct lshbloom_server lshbloom_server_t;
+
+/* indexes: n handles (same device; P <= 256) that the server uses exclusively
+ * until destroyed.  mem_budget_bytes: device memory for in-flight requests
+ * (tokens, offsets, keys, flags), allocated once here.  max_inflight: at most
+ * this many admitted requests (1..256).  Errors: ERR_ARG, ERR_OOM, ERR_CUDA. */
+LSHB_API lshb_status lshbloom_server_create(lshbloom_t *const *indexes, uint32_t n,
+                                            uint64_t mem_budget_bytes, uint32_t max_inflight,
+                                            lshbloom_server_t **out);
+
+/* Queue D documents (host offsets[D+1], host tokens) for index `index`; the
+ * flags land in host flags_out[D].  The three buffers must stay valid until
+ * the request completes.  *ticket identifies the request.  ERR_BUSY when the
+ * request alone needs more than the memory budget; ERR_CSR for decreasing
+ * offsets. */
+LSHB_API lshb_status lshbloom_server_submit(lshbloom_server_t *s, uint32_t index,
+                                            const uint64_t *offsets, const uint32_t *tokens,
+                                            uint64_t D, uint8_t *flags_out, uint64_t *ticket);
+
+/* Wait up to timeout_ms (< 0: forever) for a request.  Returns LSHB_OK when
+ * it completed (its own status otherwise), ERR_TIMEOUT when still running.
+ * latency_us (optional) receives submit-to-completion time in microseconds.
+ * A completed ticket can be waited on once. */
+LSHB_API lshb_status lshbloom_server_wait(lshbloom_server_t *s, uint64_t ticket, double timeout_ms,
+                                          double *latency_us);
+
+/* Finish every queued request, stop the worker, release the budget.  The
+ * indexes stay valid (and hold every request's insertions). NULL is a no-op. */
+LSHB_API void lshbloom_server_destroy(lshbloom_server_t *s);
+
 /* Message of the last failed call on this thread ("" if none). */
 LSHB_API const char *lshbloom_last_error(void);
 

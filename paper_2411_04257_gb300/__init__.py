@@ -14,7 +14,8 @@ import numpy as np
 from ._native import (EXEC_BATCHED, EXEC_PLAIN, INSERT_ALL, INSERT_NONDUP, Config,
                       LSHBloomError, Stats, check, lib)
 
-__all__ = ["LSHBloom", "LSHBloomError", "optimal_br", "lib", "EXEC_PLAIN", "EXEC_BATCHED"]
+__all__ = ["LSHBloom", "LSHBloomServer", "LSHBloomError", "optimal_br", "lib", "EXEC_PLAIN",
+           "EXEC_BATCHED"]
 
 
 def _is_torch(x) -> bool:
@@ -233,6 +234,56 @@ class LSHBloom:
         h = C.c_void_p()
         check(lib().lshbloom_load(path.encode(), device, C.byref(h)))
         return cls(_handle=h)
+
+
+class LSHBloomServer:
+    """Continuous-batching request server over resident indexes
+    (lshbloom_server_*).  submit() takes host arrays and returns a ticket;
+    wait() returns (flags, latency in microseconds)."""
+
+    def __init__(self, indexes, mem_budget_bytes: int = 1 << 30, max_inflight: int = 32):
+        self._indexes = list(indexes)  # keep the handles alive
+        arr = (C.c_void_p * len(self._indexes))(*[ix._h.value for ix in self._indexes])
+        h = C.c_void_p()
+        check(lib().lshbloom_server_create(arr, len(self._indexes), mem_budget_bytes,
+                                           max_inflight, C.byref(h)))
+        self._h = h
+        self._live = {}
+
+    def submit(self, index: int, offsets, tokens) -> int:
+        off = np.ascontiguousarray(offsets, dtype=np.uint64)
+        tok = np.ascontiguousarray(tokens, dtype=np.uint32)
+        D = off.size - 1
+        flags = np.zeros(max(D, 1), np.uint8)
+        t = C.c_uint64()
+        tok_p = tok.ctypes.data if tok.size else np.zeros(1, np.uint32).ctypes.data
+        check(lib().lshbloom_server_submit(self._h, index, off.ctypes.data, tok_p, D,
+                                           flags.ctypes.data, C.byref(t)))
+        self._live[t.value] = (off, tok, flags, D)
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: float = -1.0):
+        lat = C.c_double()
+        check(lib().lshbloom_server_wait(self._h, ticket, timeout_ms, C.byref(lat)))
+        off, tok, flags, D = self._live.pop(ticket)
+        return flags[:D], lat.value
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().lshbloom_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def optimal_br(T: float, P: int):

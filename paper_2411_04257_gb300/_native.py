@@ -68,6 +68,12 @@ _SIGS = {
     "lshbloom_load": (C.c_int, [C.c_char_p, C.c_int32, C.POINTER(_VP)]),
     "lshbloom_optimal_br": (C.c_int, [C.c_double, C.c_uint32, C.POINTER(C.c_uint32),
                                       C.POINTER(C.c_uint32)]),
+    "lshbloom_server_create": (C.c_int, [C.POINTER(_VP), C.c_uint32, C.c_uint64, C.c_uint32,
+                                         C.POINTER(_VP)]),
+    "lshbloom_server_submit": (C.c_int, [_VP, C.c_uint32, _VP, _VP, C.c_uint64, _VP,
+                                         C.POINTER(C.c_uint64)]),
+    "lshbloom_server_wait": (C.c_int, [_VP, C.c_uint64, C.c_double, C.POINTER(C.c_double)]),
+    "lshbloom_server_destroy": (None, [_VP]),
     "lshbloom_last_error": (C.c_char_p, []),
     "lshbloom_destroy": (None, [_VP]),
 }

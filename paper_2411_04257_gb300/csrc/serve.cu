@@ -1,0 +1,364 @@
+// Serving: a request server with continuous batching over resident indexes.
+//
+// Requests wait in one FIFO.  A worker thread admits the head of the FIFO as
+// soon as an in-flight slot and enough of the device-memory budget are free,
+// and enqueues its copy-in and its signature stage on a stream of its own, so
+// every admitted request computes at the same time as the others.  The Bloom
+// stage of an index then runs, in arrival order, for each request of that
+// index whose signatures are done: each request is judged against exactly the
+// requests submitted before it to the same index (Sec. 2.1, Sec. 4.4.2).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "runtime_internal.h"
+#include "sig_kernels.cuh"
+
+using namespace lshb;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+enum class RState { Pending, Running, Done };
+
+struct Request {
+    uint64_t ticket = 0;
+    uint32_t index = 0;
+    uint64_t D = 0, T = 0, tok0 = 0;
+    const uint64_t *h_off = nullptr;
+    const uint32_t *h_tok = nullptr;
+    uint8_t *h_flags = nullptr;
+    uint64_t bytes = 0, pool_off = 0;
+    uint64_t *d_off = nullptr;
+    uint32_t *d_tok = nullptr;
+    uint64_t *d_keys = nullptr;
+    uint8_t *d_flags = nullptr;
+    int slot = -1;
+    RState state = RState::Pending;
+    lshb_status status = LSHB_OK;
+    Clock::time_point t_submit, t_done;
+};
+
+// First-fit allocator over the budget (offsets, 256-byte granules).
+struct Pool {
+    uint8_t *base = nullptr;
+    uint64_t size = 0;
+    std::map<uint64_t, uint64_t> free_;  // offset -> length
+
+    void init(uint8_t *b, uint64_t n) {
+        base = b;
+        size = n;
+        free_.clear();
+        free_[0] = n;
+    }
+    bool alloc(uint64_t n, uint64_t *off) {
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= n) {
+                *off = it->first;
+                const uint64_t rest = it->second - n;
+                const uint64_t at = it->first + n;
+                free_.erase(it);
+                if (rest) free_[at] = rest;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(uint64_t off, uint64_t n) {
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
+
+uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
+
+}  // namespace
+
+struct lshbloom_server {
+    std::vector<lshbloom *> idx;
+    int device = 0;
+    uint32_t bands = 0;
+    Pool pool;
+    void *pool_mem = nullptr;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> events;
+    std::vector<int> free_slots;
+    std::deque<Request *> fifo;
+    std::vector<std::deque<Request *>> running;  // per index, arrival order
+    std::unordered_map<uint64_t, Request *> reqs;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::thread worker;
+    bool stop = false;
+    uint64_t next_ticket = 1;
+
+    void loop();
+    lshb_status launch(Request *r);
+    lshb_status bloom(Request *r);
+};
+
+static uint64_t request_bytes(uint64_t D, uint64_t T, uint32_t bands) {
+    return align256((D + 1) * 8) + align256(T * 4) + align256(D * bands * 8) + align256(D);
+}
+
+lshb_status lshbloom_server::launch(Request *r) {
+    cudaStream_t s = streams[r->slot];
+    uint8_t *p = pool.base + r->pool_off;
+    r->d_off = (uint64_t *)p;
+    p += align256((r->D + 1) * 8);
+    r->d_tok = (uint32_t *)p;
+    p += align256(r->T * 4);
+    r->d_keys = (uint64_t *)p;
+    p += align256(r->D * bands * 8);
+    r->d_flags = p;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(r->d_off, r->h_off, (r->D + 1) * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_fail(e, "request offsets");
+    if (r->T && (e = cudaMemcpyAsync(r->d_tok, r->h_tok + r->tok0, r->T * 4, cudaMemcpyHostToDevice, s)) !=
+                    cudaSuccess)
+        return cuda_fail(e, "request tokens");
+    lshbloom *h = idx[r->index];
+    const SigPass &ps = h->passes[0];
+    SigArgs a;
+    memset(&a, 0, sizeof a);
+    a.offsets = r->d_off;
+    a.tokens = r->d_tok;
+    a.tok_base = r->tok0;
+    a.D = r->D;
+    a.ngram = h->ngram;
+    a.P = h->P;
+    a.bands = h->bands;
+    a.rows = h->rows;
+    a.p0 = 0;
+    a.npc = ps.npc;
+    a.c = ps.c;
+    a.keys_out = r->d_keys;
+    const int ngt = ngram_template(h->ngram);
+    if (ngt == 5) e = launch_sig_ng5(ps.ppl, a, s);
+    else if (ngt == 1) e = launch_sig_ng1(ps.ppl, a, s);
+    else e = launch_sig_ng0(ps.ppl, a, s);
+    if (e != cudaSuccess) return cuda_fail(e, "request signatures");
+    if ((e = cudaEventRecord(events[r->slot], s)) != cudaSuccess) return cuda_fail(e, "event");
+    return LSHB_OK;
+}
+
+// Bloom stage of one request on its index (the worker thread only).
+lshb_status lshbloom_server::bloom(Request *r) {
+    lshbloom *h = idx[r->index];
+    std::lock_guard<std::mutex> lock(h->mu);
+    lshb_status st = ensure_chunk_scratch(h, r->D, 0, false, false);
+    if (st != LSHB_OK) return st;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(h->buf(B_KEYS).ptr, r->d_keys, r->D * h->bands * 8, cudaMemcpyDeviceToDevice,
+                             h->stream)) != cudaSuccess)
+        return cuda_fail(e, "keys");
+    if ((st = run_bloom(h, r->D, r->d_flags, h->stream)) != LSHB_OK) return st;
+    if ((e = cudaMemcpyAsync(r->h_flags, r->d_flags, r->D, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
+        return cuda_fail(e, "flags");
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(e, "sync");
+    h->docs_seen += r->D;
+    return LSHB_OK;
+}
+
+void lshbloom_server::loop() {
+    cudaSetDevice(device);
+    std::unique_lock<std::mutex> lk(mu);
+    for (;;) {
+        // admission: FIFO head while a slot and enough memory are free
+        std::vector<Request *> admitted;
+        while (!fifo.empty() && !free_slots.empty()) {
+            Request *r = fifo.front();
+            uint64_t off = 0;
+            if (!pool.alloc(r->bytes, &off)) break;
+            r->pool_off = off;
+            r->slot = free_slots.back();
+            free_slots.pop_back();
+            r->state = RState::Running;
+            fifo.pop_front();
+            running[r->index].push_back(r);
+            admitted.push_back(r);
+        }
+        bool any_running = false;
+        for (auto &q : running) any_running |= !q.empty();
+        if (stop && fifo.empty() && !any_running) break;
+        lk.unlock();
+        for (Request *r : admitted) {
+            lshb_status st = launch(r);
+            if (st != LSHB_OK) r->status = st;
+        }
+        // Bloom stage, per index in arrival order, for finished signature stages
+        std::vector<Request *> finished;
+        for (size_t i = 0; i < running.size(); ++i) {
+            for (;;) {
+                Request *r = nullptr;
+                {
+                    std::lock_guard<std::mutex> g(mu);
+                    if (running[i].empty()) break;
+                    r = running[i].front();
+                }
+                if (r->status == LSHB_OK) {
+                    const cudaError_t q = cudaEventQuery(events[r->slot]);
+                    if (q == cudaErrorNotReady) break;
+                    if (q != cudaSuccess) r->status = cuda_fail(q, "signature stage");
+                    else r->status = bloom(r);
+                } else {
+                    cudaStreamSynchronize(streams[r->slot]);
+                }
+                std::lock_guard<std::mutex> g(mu);
+                running[i].pop_front();
+                finished.push_back(r);
+            }
+        }
+        lk.lock();
+        for (Request *r : finished) {
+            r->t_done = Clock::now();
+            r->state = RState::Done;
+            pool.release(r->pool_off, r->bytes);
+            free_slots.push_back(r->slot);
+        }
+        if (!finished.empty()) cv_done.notify_all();
+        if (admitted.empty() && finished.empty()) {
+            // nothing moved: wait for a submission or poll the GPU again soon
+            cv_work.wait_for(lk, std::chrono::microseconds(50));
+        }
+    }
+}
+
+extern "C" lshb_status lshbloom_server_create(lshbloom_t *const *indexes, uint32_t n,
+                                              uint64_t mem_budget_bytes, uint32_t max_inflight,
+                                              lshbloom_server_t **out) {
+    if (!indexes || n == 0 || !out || max_inflight == 0 || max_inflight > 256 ||
+        mem_budget_bytes < 4096)
+        return fail(LSHB_ERR_ARG, "bad server arguments");
+    *out = nullptr;
+    for (uint32_t i = 0; i < n; ++i) {
+        if (!indexes[i]) return fail(LSHB_ERR_ARG, "NULL index %u", i);
+        if (indexes[i]->device != indexes[0]->device)
+            return fail(LSHB_ERR_ARG, "indexes must share one device");
+        if (indexes[i]->passes.size() != 1) return fail(LSHB_ERR_ARG, "serving needs P <= 256");
+    }
+    lshbloom_server *s = new (std::nothrow) lshbloom_server();
+    if (!s) return fail(LSHB_ERR_OOM, "host allocation");
+    s->idx.assign(indexes, indexes + n);
+    s->device = indexes[0]->device;
+    s->bands = 0;
+    for (auto *h : s->idx) s->bands = std::max(s->bands, h->bands);
+    cudaSetDevice(s->device);
+    cudaError_t e = cudaMalloc(&s->pool_mem, mem_budget_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return fail(LSHB_ERR_OOM, "server budget of %llu bytes", (unsigned long long)mem_budget_bytes);
+    }
+    s->pool.init((uint8_t *)s->pool_mem, mem_budget_bytes & ~255ull);
+    s->streams.resize(max_inflight);
+    s->events.resize(max_inflight);
+    for (uint32_t i = 0; i < max_inflight; ++i) {
+        cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking);
+        cudaEventCreateWithFlags(&s->events[i], cudaEventDisableTiming);
+        s->free_slots.push_back((int)(max_inflight - 1 - i));
+    }
+    s->running.resize(n);
+    s->worker = std::thread([s] { s->loop(); });
+    *out = s;
+    return LSHB_OK;
+}
+
+extern "C" lshb_status lshbloom_server_submit(lshbloom_server_t *s, uint32_t index,
+                                              const uint64_t *offsets, const uint32_t *tokens,
+                                              uint64_t D, uint8_t *flags_out, uint64_t *ticket) {
+    if (!s || !ticket || index >= s->idx.size()) return fail(LSHB_ERR_ARG, "bad submit arguments");
+    if (D > 0 && (!offsets || !tokens || !flags_out)) return fail(LSHB_ERR_ARG, "NULL pointer with D > 0");
+    for (uint64_t i = 0; i < D; ++i)
+        if (offsets[i + 1] < offsets[i]) return fail(LSHB_ERR_CSR, "offsets decrease at %llu", (unsigned long long)i);
+    Request *r = new (std::nothrow) Request();
+    if (!r) return fail(LSHB_ERR_OOM, "host allocation");
+    r->index = index;
+    r->D = D;
+    r->tok0 = D ? offsets[0] : 0;
+    r->T = D ? offsets[D] - offsets[0] : 0;
+    r->h_off = offsets;
+    r->h_tok = tokens;
+    r->h_flags = flags_out;
+    r->bytes = request_bytes(D, r->T, s->bands);
+    if (r->bytes > s->pool.size) {
+        delete r;
+        return fail(LSHB_ERR_BUSY, "request needs %llu bytes, the server budget is %llu",
+                    (unsigned long long)request_bytes(D, offsets[D] - offsets[0], s->bands),
+                    (unsigned long long)s->pool.size);
+    }
+    r->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        r->ticket = s->next_ticket++;
+        s->reqs[r->ticket] = r;
+        if (D == 0) {
+            r->state = RState::Done;
+            r->t_done = r->t_submit;
+        } else {
+            s->fifo.push_back(r);
+        }
+        *ticket = r->ticket;
+    }
+    s->cv_work.notify_one();
+    return LSHB_OK;
+}
+
+extern "C" lshb_status lshbloom_server_wait(lshbloom_server_t *s, uint64_t ticket, double timeout_ms,
+                                            double *latency_us) {
+    if (!s) return fail(LSHB_ERR_ARG, "NULL server");
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return fail(LSHB_ERR_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+    Request *r = it->second;
+    auto done = [r] { return r->state == RState::Done; };
+    if (timeout_ms < 0) {
+        s->cv_done.wait(lk, done);
+    } else if (!s->cv_done.wait_for(lk, std::chrono::duration<double, std::milli>(timeout_ms), done)) {
+        return fail(LSHB_ERR_TIMEOUT, "request %llu still running", (unsigned long long)ticket);
+    }
+    if (latency_us)
+        *latency_us = std::chrono::duration<double, std::micro>(r->t_done - r->t_submit).count();
+    const lshb_status st = r->status;
+    s->reqs.erase(it);
+    delete r;
+    if (st != LSHB_OK) return fail(st, "request %llu failed", (unsigned long long)ticket);
+    return LSHB_OK;
+}
+
+extern "C" void lshbloom_server_destroy(lshbloom_server_t *s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    cudaSetDevice(s->device);
+    for (auto &kv : s->reqs) delete kv.second;
+    for (auto st : s->streams) cudaStreamDestroy(st);
+    for (auto ev : s->events) cudaEventDestroy(ev);
+    if (s->pool_mem) cudaFree(s->pool_mem);
+    delete s;
+}

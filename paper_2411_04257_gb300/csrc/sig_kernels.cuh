@@ -19,7 +19,7 @@ namespace lshb {
 template <int PPL>
 struct LaneCoef {
     uint32_t a0[PPL], a1[PPL];
-    uint64_t b0[PPL], b1[PPL];  // zero-extended: the 64-bit addends of the wide multiplies
+    uint64_t b0[PPL], b1[PPL];  // 64-bit addends of the wide multiplies (b0 carries a +1, see below)
 
     __device__ __forceinline__ void load(const PermSlice &c, uint32_t npc, int lane) {
 #pragma unroll
@@ -28,19 +28,28 @@ struct LaneCoef {
             const bool on = i < npc;
             a0[t] = on ? c.a0[i] : 0u;
             a1[t] = on ? c.a1[i] : 0u;
-            b0[t] = on ? c.b0[i] : 0u;
+            b0[t] = on ? (uint64_t)c.b0[i] + 1ull : 1ull;
             b1[t] = on ? c.b1[i] : 0u;
         }
     }
 };
 
-// ((a*h + b) mod (2^61 - 1)) mod 2^32 with the addends already 64-bit.
+// ((a*h + b) mod (2^61 - 1)) mod 2^32, exact, for a = a1:a0, b = b1:b0 < 2^61 - 1
+// and h < 2^32.  With x = a h + b, work on x + 1 (the +1 rides in b0):
+//   t = a0 h + b0 + 1 < 2^64,  V = a1 h + b1 + (t >> 32) < 2^61,
+//   x + 1 = V 2^32 + (t mod 2^32);
+// 2^61 = 1 (mod p) folds it to s = (V mod 2^29) 2^32 + (t mod 2^32) + (V >> 29),
+// 1 <= s < 2^61 + 2^32, s = x + 1 (mod p).  Then x mod p = s - 1 - p [s >= 2^61],
+// whose low 32 bits are s_lo - 1 + (s >> 61) since 2^61 = 0 (mod 2^32).
+// Two wide multiplies and ALU work; written in C, the compiler's split between
+// the IMAD and ALU pipes measured faster than hand-placing the 64-bit adds and
+// shifts on the IMAD pipe (the wide multiplies already load it).
 __device__ __forceinline__ uint32_t perm_lo32w(uint32_t h, uint32_t a0, uint32_t a1, uint64_t b0,
                                                uint64_t b1) {
     const uint64_t t = (uint64_t)a0 * h + b0;
     const uint64_t V = (uint64_t)a1 * h + b1 + (t >> 32);
-    const uint64_t s1 = ((((V & 0x1fffffffull) << 32) | (uint32_t)t) + (V >> 29)) + 1ull;
-    return (uint32_t)s1 - 1u + (uint32_t)(s1 >> 61);
+    const uint64_t s = (((V & 0x1fffffffull) << 32) | (uint32_t)t) + (V >> 29);
+    return (uint32_t)s - 1u + (uint32_t)(s >> 61);
 }
 
 template <int PPL>
