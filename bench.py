@@ -41,6 +41,20 @@ SM_MAX_MHZ = 2070.0
 IMAD_PER_PERMHASH = 4       # two 32x32->64 products (lo and hi halves) per (a*h + b)
 
 
+def reduce_over_ranks(seconds: float, units: float, device=None):
+    """Whole-job timing for N independent replicas (one process per GPU):
+    the slowest rank's time and the units every rank processed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return seconds, units
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def _rank_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -298,15 +312,12 @@ def run_ours(args):
         stage[mode] = {"sig_ms": s1["sig_ms"] - s0["sig_ms"],
                        "bloom_ms": s1["bloom_ms"] - s0["bloom_ms"],
                        "sig_chunks": s1["sig_chunks"] - s0["sig_chunks"]}
-        t = torch.tensor([dt], device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dt = float(t.item())
+        dt, docs = reduce_over_ranks(dt, float(D * args.steps), dev)
+        _, ph = reduce_over_ranks(dt, float(permhashes * args.steps), dev)
         ix.reset()
         flags = ix.dedup_async(off, tok, stream=stream)
         torch.cuda.synchronize()
-        results[mode] = {"seconds": dt, "docs_per_s": D * world * args.steps / dt,
-                         "shingle_hashes_per_s": permhashes * world * args.steps / dt,
+        results[mode] = {"seconds": dt, "docs_per_s": docs / dt, "shingle_hashes_per_s": ph / dt,
                          "clocks": clocks, "dups_per_step": int(flags.sum().item())}
         ix.close()
 
@@ -337,12 +348,9 @@ def run_ours(args):
             ixe.dedup(h_off, h_tok, out=h_flags)
         barrier_sync()
         et = time.perf_counter() - t0
-        t = torch.tensor([et], device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        et = float(t.item())
+        et, docs = reduce_over_ranks(et, float(D * args.steps), dev)
         ixe.close()
-        e2e = {"value": D * world * args.steps / et, "unit": "docs/s",
+        e2e = {"value": docs / et, "unit": "docs/s",
                "h2d_bytes_per_step": (D + 1) * 8 + T * 4, "d2h_bytes_per_step": D}
         del h_tok
 
