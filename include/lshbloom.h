@@ -149,6 +149,12 @@ LSHB_API lshb_status lshbloom_dedup(lshbloom_t *h, const uint64_t *offsets, cons
 LSHB_API lshb_status lshbloom_dedup_async(lshbloom_t *h, const uint64_t *offsets, const uint32_t *tokens,
                                  uint64_t D, uint8_t *flags_out, void *stream);
 
+/* As lshbloom_dedup, and also write the band keys (Sec. 4.1) the judgement
+ * used: keys_out is host or device uint64[D][b], row-major. */
+LSHB_API lshb_status lshbloom_dedup_keys(lshbloom_t *h, const uint64_t *offsets,
+                                         const uint32_t *tokens, uint64_t D, uint8_t *flags_out,
+                                         uint64_t *keys_out);
+
 /* MinHash signatures of D documents (Sec. 2.2, Sec. 4.1), without touching the
  * filters.  sig_out: host or device uint32[D][P], row-major.  Errors as for
  * lshbloom_dedup. */

@@ -130,6 +130,15 @@ class LSHBloom:
         check(lib().lshbloom_dedup(self._h, po, pt, D, pf))
         return fl
 
+    def dedup_keys(self, offsets, tokens):
+        """(flags, band keys) of the batch: dedup that also returns the keys
+        the judgement used."""
+        po, pt, D, like, keep = self._inputs(offsets, tokens)
+        pf, fl = _out(D, None, np.uint8, "uint8", like)
+        pk, keys = _out(D, self.bands, np.uint64, "uint64", like)
+        check(lib().lshbloom_dedup_keys(self._h, po, pt, D, pf, pk))
+        return fl, keys
+
     def dedup_async(self, offsets, tokens, stream=None):
         """As dedup, device tensors only, ordered on `stream` (torch stream or
         raw cudaStream_t; default the current torch stream)."""

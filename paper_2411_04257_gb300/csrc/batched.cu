@@ -484,7 +484,8 @@ static lshb_status ensure_graph(lshbloom *h, cudaStream_t s) {
 
 lshb_status run_batched(lshbloom *h, const uint64_t *offsets, const uint32_t *tokens, uint64_t D,
                         uint8_t *flags, const std::vector<uint64_t> &off, bool off_dev,
-                        bool tok_dev, bool out_dev, cudaStream_t s) {
+                        bool tok_dev, bool out_dev, cudaStream_t s, uint64_t *keys_out,
+                        bool keys_dev) {
     // chunks: documents and (for staged or very large inputs) tokens bounded
     const uint64_t dmax = h->max_docs_batched;
     std::vector<std::pair<uint64_t, uint64_t>> chunks;
@@ -559,6 +560,9 @@ lshb_status run_batched(lshbloom *h, const uint64_t *offsets, const uint32_t *to
         BCK(cudaStreamSynchronize(s));
         float ms_k7 = 0.f;
         BCK(cudaEventElapsedTime(&ms_k7, b->ev0, b->ev1));
+        if (keys_out)
+            BCK(cudaMemcpyAsync(keys_out + lo * h->bands, h->buf(B_KEYS).ptr, Dn * h->bands * 8,
+                                keys_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
         BloomArgs A = bloom_args(h, Dn);
         A.sketch_bits_log2 = sketch_log2_for(h, b->dcap);
         uint8_t *fl = out_dev ? flags + lo : (uint8_t *)outbuf.ptr;

@@ -534,7 +534,7 @@ enum class Job { Dedup, Signatures, Keys, Hashes };
 
 static lshb_status run_batch(lshbloom *h, const uint64_t *offsets, const uint32_t *tokens,
                              uint64_t D, void *out, Job job, cudaStream_t user_stream,
-                             bool require_device) {
+                             bool require_device, uint64_t *keys_out = nullptr) {
     if (D == 0) return LSHB_OK;
     if (!offsets || !tokens || !out) return fail(LSHB_ERR_ARG, "NULL pointer with D > 0");
     std::lock_guard<std::mutex> lock(h->mu);
@@ -542,6 +542,7 @@ static lshb_status run_batch(lshbloom *h, const uint64_t *offsets, const uint32_
     const bool off_dev = is_device_pointer(offsets);
     const bool tok_dev = is_device_pointer(tokens);
     const bool out_dev = is_device_pointer(out);
+    const bool keys_dev = keys_out && is_device_pointer(keys_out);
     if (require_device && (!off_dev || !tok_dev || !out_dev))
         return fail(LSHB_ERR_ARG, "lshbloom_dedup_async takes device pointers only");
     cudaStream_t s = user_stream ? user_stream : h->stream;
@@ -549,7 +550,8 @@ static lshb_status run_batch(lshbloom *h, const uint64_t *offsets, const uint32_
     lshb_status st = host_offsets(h, offsets, D, off_dev, off);
     if (st != LSHB_OK) return st;
     if (job == Job::Dedup && h->cfg.exec_mode == LSHB_EXEC_BATCHED && h->passes.size() == 1) {
-        return run_batched(h, offsets, tokens, D, (uint8_t *)out, off, off_dev, tok_dev, out_dev, s);
+        return run_batched(h, offsets, tokens, D, (uint8_t *)out, off, off_dev, tok_dev, out_dev, s,
+                           keys_out, keys_dev);
     }
     const bool plain = h->cfg.exec_mode == LSHB_EXEC_PLAIN;
     const bool need_hash_buf = plain && job != Job::Hashes;
@@ -610,6 +612,9 @@ static lshb_status run_batch(lshbloom *h, const uint64_t *offsets, const uint32_
             if ((st = run_signatures(h, in, nullptr, nullptr, true, s)) != LSHB_OK) return st;
             CK(cudaEventRecord(h->ev_t[1], s));
             uint8_t *fl = out_dev ? (uint8_t *)out + lo : (uint8_t *)outbuf.ptr;
+            if (keys_out)
+                CK(cudaMemcpyAsync(keys_out + lo * h->bands, h->buf(B_KEYS).ptr, Dn * h->bands * 8,
+                                   keys_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
             if ((st = run_bloom(h, Dn, fl, s)) != LSHB_OK) return st;
             CK(cudaEventRecord(h->ev_t[2], s));
             CK(cudaEventSynchronize(h->ev_t[2]));
@@ -649,6 +654,14 @@ extern "C" lshb_status lshbloom_dedup(lshbloom_t *h, const uint64_t *offsets,
                                       const uint32_t *tokens, uint64_t D, uint8_t *flags_out) {
     if (!h) return fail(LSHB_ERR_ARG, "NULL handle");
     return run_batch(h, offsets, tokens, D, flags_out, Job::Dedup, nullptr, false);
+}
+
+extern "C" lshb_status lshbloom_dedup_keys(lshbloom_t *h, const uint64_t *offsets,
+                                           const uint32_t *tokens, uint64_t D, uint8_t *flags_out,
+                                           uint64_t *keys_out) {
+    if (!h) return fail(LSHB_ERR_ARG, "NULL handle");
+    if (D > 0 && !keys_out) return fail(LSHB_ERR_ARG, "NULL keys_out");
+    return run_batch(h, offsets, tokens, D, flags_out, Job::Dedup, nullptr, false, keys_out);
 }
 
 extern "C" lshb_status lshbloom_dedup_async(lshbloom_t *h, const uint64_t *offsets,

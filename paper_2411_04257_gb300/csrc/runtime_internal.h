@@ -112,7 +112,8 @@ lshb_status resolve_and_insert(lshbloom *h, const BloomArgs &A, uint8_t *flags_d
 // Batched (persistent, graph-launched) form.
 lshb_status run_batched(lshbloom *h, const uint64_t *offsets, const uint32_t *tokens, uint64_t D,
                         uint8_t *flags, const std::vector<uint64_t> &off, bool off_dev,
-                        bool tok_dev, bool out_dev, cudaStream_t s);
+                        bool tok_dev, bool out_dev, cudaStream_t s, uint64_t *keys_out,
+                        bool keys_dev);
 void destroy_batched_state(lshbloom *h);
 
 }  // namespace lshb

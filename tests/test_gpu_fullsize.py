@@ -1,0 +1,109 @@
+"""Parity at the workloads' full sizes, in the launch configuration bench.py
+times (batched form, whole batch per call, default chunking).
+
+The oracle cannot replay a million-document stream in test time, so:
+  * sampled documents: the oracle computes their band keys one by one, and
+    the keys the timed path used must equal them exactly (the longest
+    documents, split over many work items, are always in the sample);
+  * every document: a document with an exact band match against an earlier
+    inserted document (the MinHashLSH bucket rule) must be flagged, and
+    flags without one must be Bloom false positives (fill^k, ~0 here);
+  * the plain one-kernel-per-stage form gives the same flags."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lshb():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2411_04257_gb300 as L
+    L.lib()
+    return L
+
+
+def exact_bucket_hits(keys, flags):
+    """hit[i]: some band of doc i has the same key as an earlier doc that was
+    inserted (flag 0, insert-non-duplicates rule)."""
+    D, b = keys.shape
+    inserted = (flags == 0).astype(np.int64)
+    idx = np.arange(D)
+    hit = np.zeros(D, bool)
+    for j in range(b):
+        order = np.lexsort((idx, keys[:, j]))
+        ks = keys[order, j]
+        ins = inserted[order]
+        start = np.ones(D, bool)
+        start[1:] = ks[1:] != ks[:-1]
+        grp = np.cumsum(start) - 1
+        before = np.cumsum(ins) - ins
+        hit[order] |= (before - before[start][grp]) > 0
+    return hit
+
+
+def _check(lshb, oracle, spec, n_expected, calls=1, sample=200, seed=0):
+    from synth import gpu as sgpu
+    gen = sgpu.DeviceCorpus(spec)
+    ix = lshb.LSHBloom(121, 11, 11, n_expected=n_expected, fp_rate=1e-5)
+    per = spec.n_docs // calls
+    flags, keys, lens, samples = [], [], [], []
+    rnd = np.random.default_rng(seed)
+    for c in range(calls):
+        off, tok = gen.generate(c * per, per)
+        f, k = ix.dedup_keys(off, tok)
+        torch.cuda.synchronize()
+        off_h = off.cpu().numpy().view(np.uint64)
+        L = np.diff(off_h)
+        pick = set(rnd.choice(per, size=min(sample // calls, per), replace=False).tolist())
+        pick |= set(np.argsort(L)[-3:].tolist())        # the longest: split over many items
+        k_h = k.cpu().numpy().view(np.uint64)
+        for d in sorted(pick):
+            t = tok[int(off_h[d]):int(off_h[d + 1])].cpu().numpy().view(np.uint32)
+            samples.append((t, k_h[d]))
+        flags.append(f.cpu().numpy())
+        keys.append(k_h)
+        lens.append(L)
+        del off, tok
+    flags = np.concatenate(flags)
+    keys = np.concatenate(keys)
+    a, b = oracle.coefficients(1, 121)
+    for t, want_keys in samples:
+        sig = oracle.signature(t, 5, a, b)
+        assert np.array_equal(oracle.band_keys(sig, 11, 11), want_keys)
+    hit = exact_bucket_hits(keys, flags)
+    assert np.all(flags[hit] == 1), "an exact band match was not flagged"
+    extra = int(np.sum((flags == 1) & ~hit))
+    assert extra <= 2, extra
+    return ix, flags, gen
+
+
+def test_pes2o_shaped_1m(lshb, oracle):
+    from synth import corpus
+    spec = corpus.pes2o_shaped(n_docs=1_000_000)
+    ix, flags, gen = _check(lshb, oracle, spec, 39_000_000)
+    assert 100_000 < flags.sum() < 200_000
+    # the plain form agrees on the whole batch
+    off, tok = gen.generate(0, spec.n_docs)
+    ixp = lshb.LSHBloom(121, 11, 11, n_expected=39_000_000, fp_rate=1e-5, exec_mode="plain")
+    assert np.array_equal(ixp.dedup(off, tok).cpu().numpy(), flags)
+
+
+def test_pareto_batched_8m(lshb, oracle):
+    from synth import corpus
+    spec = corpus.pareto_batched(n_docs=8_000_000)
+    _, flags, _ = _check(lshb, oracle, spec, 39_000_000, sample=400)
+    assert flags.sum() > 300_000
+
+
+def test_billion_stream_prefix_three_calls(lshb, oracle):
+    """First 3M documents of the billion-document stream (sources within a
+    1M-document window), generated per call on the device, filters sized for
+    n = 1e9 (11 x 3 GB), three calls continuing one stream."""
+    from synth import corpus
+    spec = corpus.billion_stream(n_docs=3_000_000)
+    _, flags, _ = _check(lshb, oracle, spec, 1_000_000_000, calls=3, sample=300)
+    assert flags.sum() > 20_000
