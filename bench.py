@@ -41,6 +41,28 @@ SM_MAX_MHZ = 2070.0
 IMAD_PER_PERMHASH = 4       # two 32x32->64 products (lo and hi halves) per (a*h + b)
 
 
+def _measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def _probe_roofline(st):
+    """The stand-alone probe kernel of the plain form: each probe of a band key
+    reads one 32-byte sector of a filter that does not fit in L2."""
+    if not st or not st["probe_ms"] or not st["probe_sectors"]:
+        return None
+    peaks, src = _measured_peaks()
+    gbs = st["probe_sectors"] * 32 / (st["probe_ms"] / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": "k_probe_mark (plain form)", "achieved": gbs,
+            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+            "traffic": None, "peak_source": f"hbm_gbs, {src}",
+            "algorithmic_bytes": "32 B sector per probe, b*k = 187 per document"}
+
+
 def reduce_over_ranks(seconds: float, units: float, device=None):
     """Whole-job timing for N independent replicas (one process per GPU):
     the slowest rank's time and the units every rank processed."""
@@ -311,7 +333,9 @@ def run_ours(args):
         launches[mode] = s1["kernel_launches"] - s0["kernel_launches"]
         stage[mode] = {"sig_ms": s1["sig_ms"] - s0["sig_ms"],
                        "bloom_ms": s1["bloom_ms"] - s0["bloom_ms"],
-                       "sig_chunks": s1["sig_chunks"] - s0["sig_chunks"]}
+                       "sig_chunks": s1["sig_chunks"] - s0["sig_chunks"],
+                       "probe_ms": s1["probe_ms"] - s0["probe_ms"],
+                       "probe_sectors": s1["probe_sectors"] - s0["probe_sectors"]}
         dt, docs = reduce_over_ranks(dt, float(D * args.steps), dev)
         _, ph = reduce_over_ranks(dt, float(permhashes * args.steps), dev)
         ix.reset()
@@ -393,6 +417,7 @@ def run_ours(args):
                      "peak_source": "152 SMs x 64 IMAD/clk x 2070 MHz (derived)"},
         "stage_ms_per_step": {m: {"signature": v["sig_ms"] / args.steps,
                                   "bloom": v["bloom_ms"] / args.steps} for m, v in stage.items()},
+        "roofline_probe": _probe_roofline(stage.get("plain")),
         "serve": serve,
         "item_shingles": item_shingles,
         "cpu_baseline": cpu,

@@ -36,6 +36,7 @@ class Stats(C.Structure):
         ("fp_rate", C.c_double), ("fill", C.c_double * 64), ("resolve_rounds", C.c_uint64),
         ("uncertain_docs", C.c_uint64), ("kernel_launches", C.c_uint64),
         ("sig_ms", C.c_double), ("bloom_ms", C.c_double), ("sig_chunks", C.c_uint64),
+        ("probe_ms", C.c_double), ("probe_sectors", C.c_uint64),
     ]
 
 

@@ -32,8 +32,15 @@ __global__ void k_probe_mark(const __grid_constant__ BloomArgs A) {
     for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
          idx += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t j = (uint32_t)(idx % A.bands);
-        A.miss[idx] = probe_band(A.filters + (uint64_t)j * A.words_per_filter, A.keys[idx], j, A.k,
-                                 A.m_bits, A.sketch1, A.sketch2, A.sketch_bits_log2);
+        const uint32_t *F = A.filters + (uint64_t)j * A.words_per_filter;
+        if (A.k <= 24) {
+            const ProbeSeq ps(A.keys[idx], j);
+            A.miss[idx] = probe_band_unrolled<24>(F, ps, j, A.k, A.m_bits, A.sketch1, A.sketch2,
+                                                  A.sketch_bits_log2);
+        } else {
+            A.miss[idx] = probe_band(F, A.keys[idx], j, A.k, A.m_bits, A.sketch1, A.sketch2,
+                                     A.sketch_bits_log2);
+        }
     }
 }
 

@@ -43,6 +43,45 @@ __device__ __forceinline__ uint64_t sketch_index(uint64_t g, uint32_t log2n) {
 // Probe one band key against its filter F (pre-batch bits): returns the mask
 // of probes that found a clear bit, and marks each such bit in the two-level
 // sketch (first mark sets sketch1, any later mark sets sketch2).
+// For k <= KMAX all k sector loads are issued before any is used, then all
+// first-level sketch atomics, then the second level: one memory round trip
+// per phase instead of one per probe.  Positions are recomputed per phase
+// (three integer operations) rather than held in registers.
+template <int KMAX>
+__device__ __forceinline__ uint64_t probe_band_unrolled(const uint32_t *F, const ProbeSeq &ps,
+                                                        uint32_t j, uint32_t k, uint64_t m,
+                                                        uint32_t *sk1, uint32_t *sk2,
+                                                        uint32_t sk_log2) {
+    uint32_t w[KMAX];
+#pragma unroll
+    for (int u = 0; u < KMAX; ++u)
+        w[u] = (u < (int)k) ? __ldg(F + (ps.pos(u, m) >> 5)) : 0xffffffffu;
+    uint64_t miss = 0;
+#pragma unroll
+    for (int u = 0; u < KMAX; ++u)
+        if (!((w[u] >> (ps.pos(u, m) & 31)) & 1u)) miss |= 1ull << u;
+    uint32_t old[KMAX];
+#pragma unroll
+    for (int u = 0; u < KMAX; ++u) {
+        old[u] = 0;
+        if ((miss >> u) & 1ull) {
+            const uint64_t si = sketch_index((uint64_t)j * m + ps.pos(u, m), sk_log2);
+            old[u] = atomicOr(sk1 + (si >> 5), 1u << (si & 31));
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < KMAX; ++u) {
+        if ((miss >> u) & 1ull) {
+            const uint64_t si = sketch_index((uint64_t)j * m + ps.pos(u, m), sk_log2);
+            const uint32_t bit = 1u << (si & 31);
+            if (old[u] & bit) atomicOr(sk2 + (si >> 5), bit);
+        }
+    }
+    return miss;
+}
+
+// Compact form (few registers): loads in groups of 8, atomics one by one.
+// Used where the probe is a small phase of a register-heavy kernel.
 __device__ __forceinline__ uint64_t probe_band(const uint32_t *F, uint64_t key, uint32_t j,
                                                uint32_t k, uint64_t m, uint32_t *sk1, uint32_t *sk2,
                                                uint32_t sk_log2) {

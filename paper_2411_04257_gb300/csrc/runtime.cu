@@ -104,6 +104,8 @@ lshbloom::~lshbloom() {
     }
     for (int i = 0; i < 3; ++i)
         if (ev_t[i]) cudaEventDestroy(ev_t[i]);
+    for (int i = 0; i < 2; ++i)
+        if (ev_p[i]) cudaEventDestroy(ev_p[i]);
     if (counters) cudaFree(counters);
     if (host_counters) cudaFreeHost(host_counters);
     if (stream) cudaStreamDestroy(stream);
@@ -230,6 +232,7 @@ lshb_status lshb::init_handle(lshbloom *h, const lshb_config *cfg) {
         CK(cudaEventCreateWithFlags(&h->ev_stage_ready[i], cudaEventDisableTiming));
     }
     for (int i = 0; i < 3; ++i) CK(cudaEventCreate(&h->ev_t[i]));
+    for (int i = 0; i < 2; ++i) CK(cudaEventCreate(&h->ev_p[i]));
     const size_t fbytes = (size_t)h->bands * h->words_per_filter * 4;
     cudaError_t e = cudaMalloc(&h->filters, fbytes);
     if (e != cudaSuccess) {
@@ -452,11 +455,18 @@ lshb_status lshb::run_bloom(lshbloom *h, uint64_t D, uint8_t *flags_dev, cudaStr
     CK(cudaMemsetAsync(A.cand, 0, D * 8, s));
     CK(cudaMemsetAsync(A.prehit, 0, D, s));
     CK(cudaMemsetAsync(h->counters, 0, 64, s));
+    CK(cudaEventRecord(h->ev_p[0], s));
     CK(launch_probe_mark(A, s));
+    CK(cudaEventRecord(h->ev_p[1], s));
+    h->probe_pending = true;
+    h->probe_sectors += D * h->bands * h->k;
     uint32_t *ulist = (uint32_t *)h->buf(B_ULIST).ptr;
     CK(launch_classify(A, (uint32_t *)h->buf(B_BLOCKCNT).ptr, h->counters + C_NU, ulist, s));
     CK(cudaMemcpyAsync(h->host_counters, h->counters, 64, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    float ms_probe = 0.f;
+    CK(cudaEventElapsedTime(&ms_probe, h->ev_p[0], h->ev_p[1]));
+    h->t_probe_ms += ms_probe;
     return resolve_and_insert(h, A, flags_dev, s);
 }
 
@@ -743,6 +753,8 @@ extern "C" lshb_status lshbloom_stats(lshbloom_t *h, lshb_stats *out) {
     out->sig_ms = h->t_sig_ms;
     out->bloom_ms = h->t_bloom_ms;
     out->sig_chunks = h->sig_chunks;
+    out->probe_ms = h->t_probe_ms;
+    out->probe_sectors = h->probe_sectors;
     unsigned long long *cnt = (unsigned long long *)(h->counters + C_POPCOUNT);
     for (uint32_t j = 0; j < h->bands; ++j) {
         CK(cudaMemsetAsync(cnt, 0, 8, h->stream));

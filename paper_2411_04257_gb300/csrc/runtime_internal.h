@@ -84,6 +84,10 @@ struct lshbloom {
     cudaEvent_t ev_t[3] = {nullptr, nullptr, nullptr};  // stage timers
     double t_sig_ms = 0.0, t_bloom_ms = 0.0;
     uint64_t sig_chunks = 0;
+    cudaEvent_t ev_p[2] = {nullptr, nullptr};  // bracket the probe kernel (one-kernel-per-stage form)
+    double t_probe_ms = 0.0;
+    uint64_t probe_sectors = 0;                // band-key probes issued by that kernel
+    bool probe_pending = false;
 
     lshb::DevBuf &buf(lshb::BufId id) { return bufs[id]; }
     ~lshbloom();
