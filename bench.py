@@ -32,6 +32,8 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     # name: (spec factory, n_docs, n_expected, fp_rate)
     "pes2o_1m": ("pes2o_shaped", 1_000_000, 39_000_000, 1e-5),
+    # the first 100k documents of the same corpus, same filters (still > L2): profiling case
+    "pes2o_100k": ("pes2o_shaped", 100_000, 39_000_000, 1e-5),
     "plain_10k": ("plain_10k", 10_000, 10_000, 1e-5),
 }
 P, BANDS, ROWS, NGRAM = 121, 11, 11, 5

@@ -536,7 +536,6 @@ lshb_status run_batched(lshbloom *h, const uint64_t *offsets, const uint32_t *to
             dp.tok_base = off[lo];
         } else {
             if (ci == 0 && (st = issue_copy(0)) != LSHB_OK) return st;
-            if (ci + 1 < chunks.size() && (st = issue_copy(ci + 1)) != LSHB_OK) return st;
             BCK(cudaStreamWaitEvent(s, h->ev_stage_ready[ci & 1], 0));
             dp.tokens = (const uint32_t *)h->stage_tok[ci & 1].ptr;
             dp.tok_base = off[lo];
@@ -557,6 +556,9 @@ lshb_status run_batched(lshbloom *h, const uint64_t *offsets, const uint32_t *to
         BCK(cudaGraphLaunch(b->exec, s));
         count_launch(10);  // prepare, 3 scan, expand, persistent, 4 classify kernels
         BCK(cudaEventRecord(h->ev_t[1], s));
+        // Prefetch the next chunk's tokens only now, while this chunk computes:
+        // a copy call that blocks the host then no longer idles the GPU.
+        if (!tok_dev && ci + 1 < chunks.size() && (st = issue_copy(ci + 1)) != LSHB_OK) return st;
         BCK(cudaStreamSynchronize(s));
         float ms_k7 = 0.f;
         BCK(cudaEventElapsedTime(&ms_k7, b->ev0, b->ev1));

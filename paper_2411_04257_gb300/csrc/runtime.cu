@@ -597,8 +597,13 @@ static lshb_status run_batch(lshbloom *h, const uint64_t *offsets, const uint32_
         return LSHB_OK;
     };
     if (!tok_dev && !chunks.empty() && (st = issue_copy(0)) != LSHB_OK) return st;
+    // The next chunk's copy is issued once this chunk's first kernels are
+    // queued, so a copy call that blocks the host never leaves the GPU idle.
+    auto prefetch_next = [&](size_t ci) -> lshb_status {
+        if (tok_dev || ci + 1 >= chunks.size()) return LSHB_OK;
+        return issue_copy(ci + 1);
+    };
     for (size_t ci = 0; ci < chunks.size(); ++ci) {
-        if (!tok_dev && ci + 1 < chunks.size() && (st = issue_copy(ci + 1)) != LSHB_OK) return st;
         const uint64_t lo = chunks[ci].first, hi = chunks[ci].second, Dn = hi - lo;
         ChunkIn in;
         in.D = Dn;
@@ -621,6 +626,7 @@ static lshb_status run_batch(lshbloom *h, const uint64_t *offsets, const uint32_
             CK(cudaEventRecord(h->ev_t[0], s));
             if ((st = run_signatures(h, in, nullptr, nullptr, true, s)) != LSHB_OK) return st;
             CK(cudaEventRecord(h->ev_t[1], s));
+            if ((st = prefetch_next(ci)) != LSHB_OK) return st;
             uint8_t *fl = out_dev ? (uint8_t *)out + lo : (uint8_t *)outbuf.ptr;
             if (keys_out)
                 CK(cudaMemcpyAsync(keys_out + lo * h->bands, h->buf(B_KEYS).ptr, Dn * h->bands * 8,
@@ -654,6 +660,7 @@ static lshb_status run_batch(lshbloom *h, const uint64_t *offsets, const uint32_
             if (!out_dev && nt)
                 CK(cudaMemcpyAsync((uint32_t *)out + t0, ho, nt * 4, cudaMemcpyDeviceToHost, s));
         }
+        if (job != Job::Dedup && (st = prefetch_next(ci)) != LSHB_OK) return st;
         if (!tok_dev) CK(cudaEventRecord(h->ev_stage_free[ci & 1], s));
     }
     if (!require_device) CK(cudaStreamSynchronize(s));
