@@ -134,6 +134,14 @@ LSHB_API lshb_status lshbloom_create(uint32_t P, uint32_t b, uint32_t r, uint64_
 /* Create from a full configuration (see lshb_config).  Errors as above. */
 LSHB_API lshb_status lshbloom_create_ex(const lshb_config *cfg, lshbloom_t **out);
 
+/* Create the index the way the paper parameterises it: a Jaccard threshold T
+ * in (0, 1) and P permutations give (b, r) by lshbloom_optimal_br (Eqs. 1-2,
+ * Sec. 4.3); an effective false-positive rate p_eff over all b filters gives
+ * the per-filter rate p = 1 - (1 - p_eff)^(1/b) (Sec. 4.3) and the sizing of
+ * Sec. 4.5.  Other settings take lshbloom_config_default values. */
+LSHB_API lshb_status lshbloom_create_threshold(double T, uint32_t P, uint64_t n_expected,
+                                               double p_eff, lshbloom_t **out);
+
 /* Judge D documents in stream order against all earlier documents of this
  * handle (Sec. 2.1, Sec. 4.2) and insert them (Sec. 4.1, Sec. 4.4.2).
  * offsets: host or device uint64[D+1]; tokens: host or device uint32, indexed

@@ -205,6 +205,24 @@ OR_API void or_probe_positions(uint64_t key, uint32_t j, uint64_t m, uint32_t k,
     }
 }
 
+/* Blocked layout (a variant beyond the paper, after Putze, Sanders and
+ * Singler's cache-efficient Bloom filters, 2007): all k bits of a key lie in
+ * one 256-bit block of the m-bit filter (m is a multiple of 256), each bit an
+ * independent byte of a SplitMix64 word.  With x and y as above:
+ * block = floor(x * (m/256) / 2^64), w_t = mix64(y + t * 0x9e3779b97f4a7c15),
+ * q_u = 256 block + (byte u mod 8 of w_{floor(u/8)}). */
+OR_API void or_probe_positions_blocked(uint64_t key, uint32_t j, uint64_t m, uint32_t k,
+                                       uint64_t *q) {
+    uint64_t x = or_mix64(key ^ ((uint64_t)j * 0x9e3779b97f4a7c15ull));
+    uint64_t y = or_mix64(x ^ 0x6a09e667f3bcc909ull) | 1ull;
+    uint64_t nblocks = m / 256;
+    uint64_t block = (uint64_t)(((u128)x * (u128)nblocks) >> 64);
+    for (uint32_t u = 0; u < k; ++u) {
+        uint64_t w = or_mix64(y + (uint64_t)(u / 8) * 0x9e3779b97f4a7c15ull);
+        q[u] = 256 * block + ((w >> (8 * (u % 8))) & 255);
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Sizing, Sec. 4.5 and Sec. 4.3.                                            */
 /* ------------------------------------------------------------------------ */
@@ -305,6 +323,7 @@ OR_API void or_optimal_br(double T, uint32_t P, uint32_t *b_out, uint32_t *r_out
 
 typedef struct {
     uint32_t P, bands, rows, ngram, k, insert_all;
+    uint32_t layout;     /* 0: standard filter (Sec. 2.4), 1: 256-bit blocked variant */
     uint64_t m;          /* bits per filter */
     uint64_t words;      /* 64-bit words per filter */
     uint64_t *a, *b;     /* permutation coefficients */
@@ -332,6 +351,18 @@ OR_API or_index *or_index_create(uint32_t P, uint32_t bands, uint32_t rows, uint
         return NULL;
     }
     return ix;
+}
+
+/* Select the probe layout of an empty index (0 standard, 1 blocked). */
+OR_API int or_index_set_layout(or_index *ix, uint32_t layout) {
+    if (layout > 1 || (layout == 1 && ix->m % 256 != 0)) return -1;
+    ix->layout = layout;
+    return 0;
+}
+
+static void or_index_positions(const or_index *ix, uint64_t key, uint32_t j, uint64_t *q) {
+    if (ix->layout == 1) or_probe_positions_blocked(key, j, ix->m, ix->k, q);
+    else or_probe_positions(key, j, ix->m, ix->k, q);
 }
 
 OR_API void or_index_destroy(or_index *ix) {
@@ -370,7 +401,7 @@ OR_API void or_index_dedup(or_index *ix, const uint64_t *offsets, const uint32_t
         int dup = 0;
         for (uint32_t j = 0; j < ix->bands; ++j) {
             uint64_t *qj = q + (uint64_t)j * ix->k;
-            or_probe_positions(keys[j], j, ix->m, ix->k, qj);
+            or_index_positions(ix, keys[j], j, qj);
             int all_set = 1;
             for (uint32_t u = 0; u < ix->k; ++u)
                 if (!or_get_bit(ix, j, qj[u])) all_set = 0;
@@ -392,7 +423,7 @@ OR_API void or_index_dedup(or_index *ix, const uint64_t *offsets, const uint32_t
 OR_API int or_index_query_key(const or_index *ix, uint32_t j, uint64_t key) {
     uint64_t q[256];
     if (ix->k > 256) return -1;
-    or_probe_positions(key, j, ix->m, ix->k, q);
+    or_index_positions(ix, key, j, q);
     for (uint32_t u = 0; u < ix->k; ++u)
         if (!or_get_bit(ix, j, q[u])) return 0;
     return 1;
@@ -401,7 +432,7 @@ OR_API int or_index_query_key(const or_index *ix, uint32_t j, uint64_t key) {
 OR_API void or_index_insert_key(or_index *ix, uint32_t j, uint64_t key) {
     uint64_t q[256];
     if (ix->k > 256) return;
-    or_probe_positions(key, j, ix->m, ix->k, q);
+    or_index_positions(ix, key, j, q);
     for (uint32_t u = 0; u < ix->k; ++u) or_set_bit(ix, j, q[u]);
 }
 

@@ -57,6 +57,9 @@ def lib():
                 "or_band_keys": (None, [u32p, C.c_uint32, C.c_uint32, u64p]),
                 "or_probe_positions": (None, [C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint32,
                                               u64p]),
+                "or_probe_positions_blocked": (None, [C.c_uint64, C.c_uint32, C.c_uint64,
+                                                      C.c_uint32, u64p]),
+                "or_index_set_layout": (C.c_int, [C.c_void_p, C.c_uint32]),
                 "or_p_from_effective": (C.c_double, [C.c_double, C.c_uint32]),
                 "or_effective_from_p": (C.c_double, [C.c_double, C.c_uint32]),
                 "or_sizing": (None, [C.c_uint64, C.c_double, u64p, C.POINTER(C.c_uint32)]),
@@ -158,6 +161,12 @@ def probe_positions(key: int, j: int, m: int, k: int) -> np.ndarray:
     return q
 
 
+def probe_positions_blocked(key: int, j: int, m: int, k: int) -> np.ndarray:
+    q = np.zeros(k, np.uint64)
+    lib().or_probe_positions_blocked(key, j, m, k, _p(q, C.c_uint64))
+    return q
+
+
 def batch_signatures(offsets, tokens, n: int, a, b) -> np.ndarray:
     off = _u64(offsets)
     tok = _u32(tokens)
@@ -234,7 +243,8 @@ class OracleIndex:
     def __init__(self, P: int, bands: int, rows: int, n_expected: int = 10_000,
                  fp_rate: float = 1e-5, ngram: int = 5, seed: int = 1,
                  insert_all: bool = False, fp_is_effective: bool = False,
-                 m: int | None = None, k: int | None = None, a=None, b=None):
+                 m: int | None = None, k: int | None = None, a=None, b=None,
+                 layout: int = 0):
         p = p_from_effective(fp_rate, bands) if fp_is_effective else fp_rate
         mm, kk = sizing(n_expected, p)
         self.m = int(m) if m is not None else mm
@@ -248,6 +258,8 @@ class OracleIndex:
                                         1 if insert_all else 0)
         if not self._h:
             raise ValueError("oracle index: bad parameters")
+        if layout and lib().or_index_set_layout(self._h, layout) != 0:
+            raise ValueError("oracle index: bad layout")
 
     def close(self):
         if getattr(self, "_h", None):

@@ -239,6 +239,14 @@ class LSHBloom:
         check(lib().lshbloom_save(self._h, path.encode()))
 
     @classmethod
+    def from_threshold(cls, T: float, P: int, n_expected: int, p_eff: float) -> "LSHBloom":
+        """(b, r) from the Jaccard threshold (Eqs. 1-2), per-filter rate from
+        the effective rate over all bands (Sec. 4.3)."""
+        h = C.c_void_p()
+        check(lib().lshbloom_create_threshold(T, P, n_expected, p_eff, C.byref(h)))
+        return cls(_handle=h)
+
+    @classmethod
     def load(cls, path: str, device: int = -1) -> "LSHBloom":
         h = C.c_void_p()
         check(lib().lshbloom_load(path.encode(), device, C.byref(h)))

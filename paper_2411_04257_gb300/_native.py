@@ -55,6 +55,8 @@ _SIGS = {
     "lshbloom_create": (C.c_int, [C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint64, C.c_double,
                                   C.POINTER(_VP)]),
     "lshbloom_create_ex": (C.c_int, [C.POINTER(Config), C.POINTER(_VP)]),
+    "lshbloom_create_threshold": (C.c_int, [C.c_double, C.c_uint32, C.c_uint64, C.c_double,
+                                            C.POINTER(_VP)]),
     "lshbloom_dedup": (C.c_int, [_VP, _VP, _VP, C.c_uint64, _VP]),
     "lshbloom_dedup_async": (C.c_int, [_VP, _VP, _VP, C.c_uint64, _VP, _VP]),
     "lshbloom_dedup_keys": (C.c_int, [_VP, _VP, _VP, C.c_uint64, _VP, _VP]),

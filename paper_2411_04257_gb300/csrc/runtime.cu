@@ -276,6 +276,23 @@ extern "C" lshb_status lshbloom_create(uint32_t P, uint32_t b, uint32_t r, uint6
     return lshbloom_create_ex(&c, out);
 }
 
+extern "C" lshb_status lshbloom_create_threshold(double T, uint32_t P, uint64_t n_expected,
+                                                 double p_eff, lshbloom_t **out) {
+    if (!out) return fail(LSHB_ERR_ARG, "NULL out");
+    uint32_t b = 0, r = 0;
+    lshb_status st = lshbloom_optimal_br(T, P, &b, &r);
+    if (st != LSHB_OK) return st;
+    lshb_config c;
+    lshbloom_config_default(&c);
+    c.num_perm = P;
+    c.bands = b;
+    c.rows = r;
+    c.n_expected = n_expected;
+    c.fp_rate = p_eff;
+    c.fp_is_effective = 1;
+    return lshbloom_create_ex(&c, out);
+}
+
 extern "C" void lshbloom_destroy(lshbloom_t *h) { delete h; }
 
 // ---- pointers and chunk planning ---------------------------------------------------

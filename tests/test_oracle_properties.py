@@ -172,3 +172,81 @@ def test_batch_split_does_not_change_flags(oracle):
         parts.append(ix.dedup(off[s:e + 1], toks))
     assert np.array_equal(np.concatenate(parts), whole)
     assert whole.sum() > 100
+
+
+# --- the blocked layout (a variant beyond the paper) ---------------------------
+
+def _blocked_fp_model(n, m, k, B=256):
+    """Blocked Bloom filter with k independent positions per key inside one
+    B-bit block (Putze, Sanders, Singler 2007), exact under that model: keys
+    per block ~ Poisson(n B / m); a block hit by i keys has Z set bits, the
+    occupancy of i k draws into B cells; a query with D distinct positions is
+    a false positive with probability C(Z, D) / C(B, D)."""
+    def occupancy(draws):
+        d = [0.0] * (B + 1)
+        d[0] = 1.0
+        for _ in range(draws):
+            nd = [0.0] * (B + 1)
+            for z, p in enumerate(d):
+                if p:
+                    nd[z] += p * z / B
+                    if z < B:
+                        nd[z + 1] += p * (B - z) / B
+            d = nd
+        return d
+    lam = n * B / m
+    dq = occupancy(k)[:k + 1]
+    tot = 0.0
+    for i in range(int(4 * lam) + 40):
+        w = math.exp(-lam + i * math.log(lam) - math.lgamma(i + 1))
+        if w < 1e-14:
+            continue
+        s = 0.0
+        for z, pz in enumerate(occupancy(i * k)):
+            if pz > 1e-16:
+                s += pz * sum(pd * math.comb(z, D) / math.comb(B, D)
+                              for D, pd in enumerate(dq) if pd and D <= z)
+        tot += w * s
+    return tot
+
+
+def test_blocked_positions_share_one_block(oracle):
+    rnd = np.random.default_rng(4)
+    m = 1 << 20
+    blocks = []
+    for _ in range(3000):
+        key = int(rnd.integers(0, 2**63))
+        j = int(rnd.integers(0, 11))
+        q = oracle.probe_positions_blocked(key, j, m, 17)
+        assert len(set((q >> 8).tolist())) == 1 and np.all(q < m)
+        x = oracle.mix64(key ^ ((j * 0x9E3779B97F4A7C15) % 2**64))
+        assert int(q[0] >> 8) == x >> (64 - 12)     # m/256 = 2^12 blocks: the top bits of x
+        blocks.append(int(q[0] >> 8))
+    counts = np.bincount(np.array(blocks) * 64 // 4096, minlength=64)
+    exp = 3000 / 64
+    assert float(((counts - exp) ** 2 / exp).sum()) < 120.0
+
+
+@pytest.mark.parametrize("fp", [1e-5, 1e-3])
+def test_blocked_false_positive_closed_form(oracle, fp):
+    n = 100_000
+    ix = oracle.OracleIndex(11, 11, 1, n_expected=n, fp_rate=fp, layout=1)
+    rnd = np.random.default_rng(31)
+    keys = rnd.integers(0, 2**63, size=n, dtype=np.uint64) * np.uint64(2) + np.uint64(1)
+    ix.insert_keys(0, keys)
+    assert ix.query_keys(0, keys).all()           # still no false negatives
+    fresh = rnd.integers(0, 2**63, size=3_000_000, dtype=np.uint64) * np.uint64(2)
+    rate = float(ix.query_keys(0, fresh).mean())
+    want = _blocked_fp_model(n, ix.m, ix.k)
+    std = (1 - math.exp(-ix.k * n / ix.m)) ** ix.k
+    assert abs(rate / want - 1) < 0.25, (rate, want)
+    assert rate > 1.5 * std                       # blocking costs accuracy at equal m
+
+
+def test_blocked_stream_semantics(oracle):
+    doc = np.arange(100, 400, dtype=np.uint32)
+    off, toks = _csr([doc, doc, np.arange(5000, 5300, dtype=np.uint32)])
+    ix = oracle.OracleIndex(121, 11, 11, layout=1)
+    assert ix.dedup(off, toks).tolist() == [0, 1, 0]
+    for j in range(11):
+        assert ix.popcount(j) <= 2 * 17
