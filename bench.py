@@ -315,9 +315,13 @@ def run_ours(args):
     launches = {}
     stage = {}
     item_shingles = None
-    for mode in (["batched", "plain"] if not args.skip_plain else ["batched"]):
-        ix = LSHBloom(P, BANDS, ROWS, n_expected=nexp, fp_rate=fp, ngram=NGRAM, exec_mode=mode,
-                      device=local)
+    modes = ["batched", "plain"] if not args.skip_plain else ["batched"]
+    if args.blocked:
+        modes += ["batched/blocked", "plain/blocked"]
+    for mode in modes:
+        ix = LSHBloom(P, BANDS, ROWS, n_expected=nexp, fp_rate=fp, ngram=NGRAM,
+                      exec_mode=mode.split("/")[0], device=local,
+                      bloom_layout="blocked" if mode.endswith("/blocked") else "standard")
 
         def step():
             ix.reset()
@@ -420,6 +424,11 @@ def run_ours(args):
         "stage_ms_per_step": {m: {"signature": v["sig_ms"] / args.steps,
                                   "bloom": v["bloom_ms"] / args.steps} for m, v in stage.items()},
         "roofline_probe": _probe_roofline(stage.get("plain")),
+        "blocked_layout": ({"batched_docs_per_s": results["batched/blocked"]["docs_per_s"],
+                            "plain_docs_per_s": results["plain/blocked"]["docs_per_s"],
+                            "dups_per_step": results["batched/blocked"]["dups_per_step"],
+                            "roofline_probe": _probe_roofline(stage["plain/blocked"])}
+                           if args.blocked else None),
         "serve": serve,
         "item_shingles": item_shingles,
         "cpu_baseline": cpu,
@@ -442,6 +451,8 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-serve", action="store_true")
+    ap.add_argument("--blocked", action="store_true",
+                    help="also measure the 256-bit blocked filter layout (both forms)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

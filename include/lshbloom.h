@@ -76,6 +76,14 @@ typedef enum {
 
 typedef enum { LSHB_INSERT_NONDUP = 0, LSHB_INSERT_ALL = 1 } lshb_insert_mode;
 
+/* Filter layout.  STANDARD is the paper's filter (Sec. 2.4): k positions over
+ * all m bits.  BLOCKED is a variant beyond the paper (after Putze, Sanders and
+ * Singler 2007): all k positions of a key inside one 256-bit block, each an
+ * independent byte of a SplitMix64 word of y (y as for the standard layout),
+ * block = high64(x * m/256); one 32-byte sector per probed key instead of k,
+ * at a higher false-positive rate for the same m and k. */
+typedef enum { LSHB_BLOOM_STANDARD = 0, LSHB_BLOOM_BLOCKED = 1 } lshb_bloom_layout;
+
 typedef enum {
     LSHB_EXEC_PLAIN = 0,   /* one kernel per stage */
     LSHB_EXEC_BATCHED = 1  /* persistent fused kernel over a work queue, graph-launched */
@@ -98,7 +106,8 @@ typedef struct {
     uint64_t max_batch_docs;  /* docs per internal chunk, 0 = default (262144) */
     uint64_t max_batch_tokens;/* tokens per internal chunk, 0 = default (2^28) */
     uint32_t item_shingles;   /* batched mode: shingles per work item, 0 = autotuned */
-    uint32_t reserved[7];
+    uint32_t bloom_layout;    /* lshb_bloom_layout (default STANDARD) */
+    uint32_t reserved[6];
 } lshb_config;
 
 typedef struct {

@@ -23,7 +23,7 @@ class Config(C.Structure):
         ("perm_a", C.POINTER(C.c_uint64)), ("perm_b", C.POINTER(C.c_uint64)),
         ("exec_mode", C.c_uint32), ("device", C.c_int32), ("max_batch_docs", C.c_uint64),
         ("max_batch_tokens", C.c_uint64), ("item_shingles", C.c_uint32),
-        ("reserved", C.c_uint32 * 7),
+        ("bloom_layout", C.c_uint32), ("reserved", C.c_uint32 * 6),
     ]
 
 

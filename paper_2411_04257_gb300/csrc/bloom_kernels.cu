@@ -34,11 +34,11 @@ __global__ void k_probe_mark(const __grid_constant__ BloomArgs A) {
         const uint32_t j = (uint32_t)(idx % A.bands);
         const uint32_t *F = A.filters + (uint64_t)j * A.words_per_filter;
         if (A.k <= 24) {
-            const ProbeSeq ps(A.keys[idx], j);
+            const ProbeSeq ps(A.keys[idx], j, A.m_bits, A.blocked);
             A.miss[idx] = probe_band_unrolled<24>(F, ps, j, A.k, A.m_bits, A.sketch1, A.sketch2,
                                                   A.sketch_bits_log2);
         } else {
-            A.miss[idx] = probe_band(F, A.keys[idx], j, A.k, A.m_bits, A.sketch1, A.sketch2,
+            A.miss[idx] = probe_band(F, A.keys[idx], j, A.k, A.m_bits, A.blocked, A.sketch1, A.sketch2,
                                      A.sketch_bits_log2);
         }
     }
@@ -59,13 +59,13 @@ __global__ void k_classify(const __grid_constant__ BloomArgs A) {
             A.prehit[d] = 1;
             continue;
         }
-        const ProbeSeq ps(A.keys[idx], j);
+        const ProbeSeq ps(A.keys[idx], j, A.m_bits, A.blocked);
         bool all = true;
         uint64_t mm = miss;
         while (mm && all) {
             const uint32_t u = __ffsll((long long)mm) - 1;
             mm &= mm - 1;
-            const uint64_t g = (uint64_t)j * A.m_bits + ps.pos(u, A.m_bits);
+            const uint64_t g = (uint64_t)j * A.m_bits + ps.pos(u);
             const uint64_t si = sketch_index(g, A.sketch_bits_log2);
             all = (__ldg(A.sketch2 + (si >> 5)) >> (si & 31)) & 1u;
         }
@@ -194,12 +194,12 @@ __global__ void k_rk_insert(const __grid_constant__ BloomArgs A, const uint32_t 
         const uint64_t d = ulist[idx / A.bands];
         const uint32_t j = (uint32_t)(idx % A.bands);
         if (!((A.cand[d] >> j) & 1ull)) continue;
-        const ProbeSeq ps(A.keys[d * A.bands + j], j);
+        const ProbeSeq ps(A.keys[d * A.bands + j], j, A.m_bits, A.blocked);
         uint64_t mm = A.miss[d * A.bands + j];
         while (mm) {
             const uint32_t u = __ffsll((long long)mm) - 1;
             mm &= mm - 1;
-            const uint64_t g = (uint64_t)j * A.m_bits + ps.pos(u, A.m_bits);
+            const uint64_t g = (uint64_t)j * A.m_bits + ps.pos(u);
             if (!ht_insert(T.keys, T.mask, g)) atomicOr(A.error, kErrTableFull);
         }
     }
@@ -217,11 +217,11 @@ __global__ void k_fixed_setters(const __grid_constant__ BloomArgs A, ResolveTabl
         const uint32_t j = (uint32_t)(idx % A.bands);
         uint64_t mm = A.miss[idx];
         if (!mm) continue;
-        const ProbeSeq ps(A.keys[idx], j);
+        const ProbeSeq ps(A.keys[idx], j, A.m_bits, A.blocked);
         while (mm) {
             const uint32_t u = __ffsll((long long)mm) - 1;
             mm &= mm - 1;
-            const uint64_t g = (uint64_t)j * A.m_bits + ps.pos(u, A.m_bits);
+            const uint64_t g = (uint64_t)j * A.m_bits + ps.pos(u);
             const uint32_t s = ht_find(T.keys, T.mask, g);
             if (s != kNone) atomicMin(T.first_fixed + s, (uint32_t)d);
         }
@@ -237,11 +237,11 @@ __global__ void k_cache_slots(const __grid_constant__ BloomArgs A, const uint32_
         const uint64_t d = ulist[idx / A.bands];
         const uint32_t j = (uint32_t)(idx % A.bands);
         const uint64_t miss = A.miss[d * A.bands + j];
-        const ProbeSeq ps(A.keys[d * A.bands + j], j);
+        const ProbeSeq ps(A.keys[d * A.bands + j], j, A.m_bits, A.blocked);
         uint32_t *out = T.slots + idx * A.k;
         for (uint32_t u = 0; u < A.k; ++u) {
             uint32_t s = kNone;
-            if ((miss >> u) & 1ull) s = ht_find(T.keys, T.mask, (uint64_t)j * A.m_bits + ps.pos(u, A.m_bits));
+            if ((miss >> u) & 1ull) s = ht_find(T.keys, T.mask, (uint64_t)j * A.m_bits + ps.pos(u));
             out[u] = s;
         }
     }
@@ -348,12 +348,12 @@ __global__ void k_insert(const __grid_constant__ BloomArgs A, const uint8_t *ins
         uint64_t mm = A.miss[idx];
         if (!mm) continue;
         const uint32_t j = (uint32_t)(idx % A.bands);
-        const ProbeSeq ps(A.keys[idx], j);
+        const ProbeSeq ps(A.keys[idx], j, A.m_bits, A.blocked);
         uint32_t *F = A.filters + (uint64_t)j * A.words_per_filter;
         while (mm) {
             const uint32_t u = __ffsll((long long)mm) - 1;
             mm &= mm - 1;
-            const uint64_t q = ps.pos(u, A.m_bits);
+            const uint64_t q = ps.pos(u);
             atomicOr(F + (q >> 5), 1u << (q & 31));
         }
     }

@@ -13,6 +13,7 @@ struct BloomArgs {
     uint64_t D;
     const uint64_t *D_dev;      // when set, the batch size is read from device memory
     uint32_t bands, k;
+    uint32_t blocked;           // 1: 256-bit blocked filter layout
     uint64_t m_bits, words_per_filter;
     uint32_t *filters;          // bands x words_per_filter
     const uint64_t *keys;       // D x bands
@@ -55,24 +56,24 @@ __device__ __forceinline__ uint64_t probe_band_unrolled(const uint32_t *F, const
     uint32_t w[KMAX];
 #pragma unroll
     for (int u = 0; u < KMAX; ++u)
-        w[u] = (u < (int)k) ? __ldg(F + (ps.pos(u, m) >> 5)) : 0xffffffffu;
+        w[u] = (u < (int)k) ? __ldg(F + (ps.pos(u) >> 5)) : 0xffffffffu;
     uint64_t miss = 0;
 #pragma unroll
     for (int u = 0; u < KMAX; ++u)
-        if (!((w[u] >> (ps.pos(u, m) & 31)) & 1u)) miss |= 1ull << u;
+        if (!((w[u] >> (ps.pos(u) & 31)) & 1u)) miss |= 1ull << u;
     uint32_t old[KMAX];
 #pragma unroll
     for (int u = 0; u < KMAX; ++u) {
         old[u] = 0;
         if ((miss >> u) & 1ull) {
-            const uint64_t si = sketch_index((uint64_t)j * m + ps.pos(u, m), sk_log2);
+            const uint64_t si = sketch_index((uint64_t)j * m + ps.pos(u), sk_log2);
             old[u] = atomicOr(sk1 + (si >> 5), 1u << (si & 31));
         }
     }
 #pragma unroll
     for (int u = 0; u < KMAX; ++u) {
         if ((miss >> u) & 1ull) {
-            const uint64_t si = sketch_index((uint64_t)j * m + ps.pos(u, m), sk_log2);
+            const uint64_t si = sketch_index((uint64_t)j * m + ps.pos(u), sk_log2);
             const uint32_t bit = 1u << (si & 31);
             if (old[u] & bit) atomicOr(sk2 + (si >> 5), bit);
         }
@@ -83,16 +84,16 @@ __device__ __forceinline__ uint64_t probe_band_unrolled(const uint32_t *F, const
 // Compact form (few registers): loads in groups of 8, atomics one by one.
 // Used where the probe is a small phase of a register-heavy kernel.
 __device__ __forceinline__ uint64_t probe_band(const uint32_t *F, uint64_t key, uint32_t j,
-                                               uint32_t k, uint64_t m, uint32_t *sk1, uint32_t *sk2,
-                                               uint32_t sk_log2) {
-    const ProbeSeq ps(key, j);
+                                               uint32_t k, uint64_t m, bool blocked, uint32_t *sk1,
+                                               uint32_t *sk2, uint32_t sk_log2) {
+    const ProbeSeq ps(key, j, m, blocked);
     uint64_t miss = 0;
     for (uint32_t u0 = 0; u0 < k; u0 += 8) {
         uint64_t q[8];
         uint32_t w[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            q[i] = ps.pos(u0 + i, m);
+            q[i] = ps.pos(u0 + i);
             w[i] = (u0 + i < k) ? __ldg(F + (q[i] >> 5)) : 0xffffffffu;
         }
 #pragma unroll
@@ -103,7 +104,7 @@ __device__ __forceinline__ uint64_t probe_band(const uint32_t *F, uint64_t key, 
     while (mm) {
         const uint32_t u = __ffsll((long long)mm) - 1;
         mm &= mm - 1;
-        const uint64_t si = sketch_index((uint64_t)j * m + ps.pos(u, m), sk_log2);
+        const uint64_t si = sketch_index((uint64_t)j * m + ps.pos(u), sk_log2);
         const uint32_t bit = 1u << (si & 31);
         const uint32_t old = atomicOr(sk1 + (si >> 5), bit);
         if (old & bit) atomicOr(sk2 + (si >> 5), bit);

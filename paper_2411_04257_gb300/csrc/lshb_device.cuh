@@ -133,14 +133,23 @@ __device__ __forceinline__ uint32_t perm_lo32(uint32_t h, uint32_t a0, uint32_t 
     return (uint32_t)s1 - 1u + (uint32_t)(s1 >> 61);
 }
 
-// Double-hashing probe sequence of one band key (library convention).
+// Probe sequence of one band key (library convention).  Standard layout:
+// Kirsch-Mitzenmacher double hashing over the m bits.  Blocked layout (the
+// variant beyond the paper): one 256-bit block per key, each position an
+// independent byte of a SplitMix64 word.
 struct ProbeSeq {
-    uint64_t x, y;
-    __device__ __forceinline__ ProbeSeq(uint64_t key, uint32_t band) {
+    uint64_t x, y, m, base;  // base: first bit of the key's block, ~0 for the standard layout
+    __device__ __forceinline__ ProbeSeq(uint64_t key, uint32_t band, uint64_t m_bits, bool blocked) {
         x = mix64(key ^ ((uint64_t)band * kGolden));
         y = mix64(x ^ kProbeSalt) | 1ull;
+        m = m_bits;
+        base = blocked ? (__umul64hi(x, m_bits >> 8) << 8) : ~0ull;
     }
-    __device__ __forceinline__ uint64_t pos(uint32_t u, uint64_t m) const {
+    __device__ __forceinline__ uint64_t pos(uint32_t u) const {
+        if (base != ~0ull) {
+            const uint64_t w = mix64(y + (uint64_t)(u >> 3) * kGolden);
+            return base + ((w >> (8 * (u & 7))) & 255);
+        }
         return __umul64hi(x + (uint64_t)u * y, m);
     }
 };

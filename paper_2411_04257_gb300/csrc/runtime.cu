@@ -145,6 +145,7 @@ static lshb_status validate_config(const lshb_config *c) {
     if (!(c->fp_rate > 0.0 && c->fp_rate < 1.0)) return fail(LSHB_ERR_ARG, "fp_rate must be in (0,1)");
     if (c->insert_mode > 1) return fail(LSHB_ERR_ARG, "bad insert_mode");
     if (c->exec_mode > 1) return fail(LSHB_ERR_ARG, "bad exec_mode");
+    if (c->bloom_layout > 1) return fail(LSHB_ERR_ARG, "bad bloom_layout");
     if (c->item_shingles != 0 && (c->item_shingles < 64 || c->item_shingles > (1u << 20)))
         return fail(LSHB_ERR_ARG, "item_shingles must be 0 (autotuned) or 64..2^20");
     if ((c->perm_a == nullptr) != (c->perm_b == nullptr))
@@ -199,6 +200,7 @@ lshb_status lshb::init_handle(lshbloom *h, const lshb_config *cfg) {
     h->rows = cfg->rows;
     h->ngram = cfg->ngram;
     h->insert_all = cfg->insert_mode == LSHB_INSERT_ALL;
+    h->blocked = cfg->bloom_layout == LSHB_BLOOM_BLOCKED;
     h->p = cfg->fp_is_effective ? 1.0 - std::pow(1.0 - cfg->fp_rate, 1.0 / (double)cfg->bands)
                                 : cfg->fp_rate;
     if (!(h->p > 0.0 && h->p < 1.0)) return fail(LSHB_ERR_ARG, "per-filter rate out of range");
@@ -444,6 +446,7 @@ BloomArgs lshb::bloom_args(lshbloom *h, uint64_t D) {
     b.D = D;
     b.bands = h->bands;
     b.k = h->k;
+    b.blocked = h->blocked ? 1u : 0u;
     b.m_bits = h->m;
     b.words_per_filter = h->words_per_filter;
     b.filters = h->filters;
@@ -794,7 +797,7 @@ extern "C" lshb_status lshbloom_stats(lshbloom_t *h, lshb_stats *out) {
 namespace {
 struct FileHeader {
     char magic[8];            // "LSHBLOOM"
-    uint32_t version, P, bands, rows, ngram, k, insert_mode, reserved0;
+    uint32_t version, P, bands, rows, ngram, k, insert_mode, bloom_layout;
     uint64_t n_expected, seed, m_bits, words_per_filter, docs_seen, dups_seen;
     double fp_rate_cfg, p;
     int32_t fp_is_effective, reserved1;
@@ -811,6 +814,7 @@ extern "C" lshb_status lshbloom_save(lshbloom_t *h, const char *path) {
     hd.version = 1;
     hd.P = h->P; hd.bands = h->bands; hd.rows = h->rows; hd.ngram = h->ngram; hd.k = h->k;
     hd.insert_mode = h->cfg.insert_mode;
+    hd.bloom_layout = h->cfg.bloom_layout;
     hd.n_expected = h->cfg.n_expected; hd.seed = h->cfg.seed; hd.m_bits = h->m;
     hd.words_per_filter = h->words_per_filter; hd.docs_seen = h->docs_seen;
     hd.dups_seen = h->dups_seen; hd.fp_rate_cfg = h->cfg.fp_rate; hd.p = h->p;
@@ -856,6 +860,7 @@ extern "C" lshb_status lshbloom_load(const char *path, int32_t device, lshbloom_
     c.num_perm = hd.P; c.bands = hd.bands; c.rows = hd.rows; c.ngram = hd.ngram;
     c.n_expected = hd.n_expected; c.fp_rate = hd.fp_rate_cfg; c.fp_is_effective = hd.fp_is_effective;
     c.insert_mode = hd.insert_mode; c.seed = hd.seed; c.perm_a = a.data(); c.perm_b = b.data();
+    c.bloom_layout = hd.bloom_layout;
     c.device = device;
     lshbloom_t *h = nullptr;
     lshb_status st = lshbloom_create_ex(&c, &h);

@@ -62,6 +62,7 @@ struct lshbloom {
     int device = -1;
     uint32_t P = 0, bands = 0, rows = 0, ngram = 0, k = 0;
     bool insert_all = false;
+    bool blocked = false;  // 256-bit blocked filter layout
     double p = 0.0;
     uint64_t m = 0, words_per_filter = 0;
     std::vector<uint64_t> a, b;

@@ -183,6 +183,27 @@ def test_empty_short_and_long_documents(lshb, oracle):
     assert want[2] == 1 and want[3] == 1 and want[6] == 1 and want[-1] == 1
 
 
+@pytest.mark.parametrize("exec_mode", ["batched", "plain"])
+def test_blocked_layout(lshb, oracle, corpus, exec_mode, tmp_path):
+    """The 256-bit blocked filter layout against the oracle's blocked mode:
+    flags and every filter bit, then a save/load continuation."""
+    off, tok = _small_corpus(corpus, n=1600, dup_frac=0.4)
+    ix = lshb.LSHBloom(121, 11, 11, n_expected=1600, fp_rate=1e-4, bloom_layout="blocked",
+                       exec_mode=exec_mode, max_batch_docs=700)
+    ref = oracle.OracleIndex(121, 11, 11, n_expected=1600, fp_rate=1e-4, layout=1)
+    got = ix.dedup(*_dev(off[:1001], tok)).cpu().numpy()
+    path = str(tmp_path / "blocked.lshb")
+    ix.save(path)
+    ix2 = lshb.LSHBloom.load(path)
+    got = np.concatenate([got, ix2.dedup(*_dev(off[1000:], tok)).cpu().numpy()])
+    want = ref.dedup(off, tok)
+    assert np.array_equal(got, want)
+    assert want.sum() > 100
+    for j in range(11):
+        fb = ix2.filter_bytes(j)
+        assert np.array_equal(fb, ref.filter_bytes(j))
+
+
 @pytest.mark.parametrize("ngram", [1, 7])
 def test_dedup_other_ngrams(lshb, oracle, corpus, ngram):
     off, tok = _small_corpus(corpus, n=800)
