@@ -62,7 +62,8 @@ def _probe_roofline(st):
     return {"bound": "hbm", "kernel": "k_probe_mark (plain form)", "achieved": gbs,
             "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
             "traffic": None, "peak_source": f"hbm_gbs, {src}",
-            "algorithmic_bytes": "32 B sector per probe, b*k = 187 per document"}
+            "algorithmic_bytes": "32 B per addressed sector: b*k = 187 per document "
+                                 "(standard layout), b = 11 (blocked layout)"}
 
 
 def reduce_over_ranks(seconds: float, units: float, device=None):

@@ -125,7 +125,8 @@ typedef struct {
     double bloom_ms;          /* device time in the Bloom stage (CUDA events) */
     uint64_t sig_chunks;      /* signature-stage launches timed in sig_ms */
     double probe_ms;          /* device time of the stand-alone probe kernel (plain form) */
-    uint64_t probe_sectors;   /* probes (one 32-byte sector each) that kernel issued */
+    uint64_t probe_sectors;   /* 32-byte sectors that kernel's probes address (k per band key,
+                                 one per band key in the blocked layout) */
 } lshb_stats;
 
 /* Fill *cfg with defaults: P=121, b=11, r=11, n=5, n_expected=10000,

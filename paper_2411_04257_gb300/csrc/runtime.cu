@@ -479,7 +479,9 @@ lshb_status lshb::run_bloom(lshbloom *h, uint64_t D, uint8_t *flags_dev, cudaStr
     CK(launch_probe_mark(A, s));
     CK(cudaEventRecord(h->ev_p[1], s));
     h->probe_pending = true;
-    h->probe_sectors += D * h->bands * h->k;
+    // distinct 32-byte sectors the probes address: k per band key, or one
+    // (the key's block) in the blocked layout
+    h->probe_sectors += D * h->bands * (h->blocked ? 1u : h->k);
     uint32_t *ulist = (uint32_t *)h->buf(B_ULIST).ptr;
     CK(launch_classify(A, (uint32_t *)h->buf(B_BLOCKCNT).ptr, h->counters + C_NU, ulist, s));
     CK(cudaMemcpyAsync(h->host_counters, h->counters, 64, cudaMemcpyDeviceToHost, s));
