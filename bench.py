@@ -317,12 +317,15 @@ def run_ours(args):
     stage = {}
     item_shingles = None
     modes = ["batched", "plain"] if not args.skip_plain else ["batched"]
-    if args.blocked:
-        modes += ["batched/blocked", "plain/blocked"]
+    if args.variants:
+        modes += ["batched/blocked", "plain/blocked", "batched/exact", "plain/exact"]
+    index_bytes = {}
     for mode in modes:
+        layout = mode.split("/")[1] if "/" in mode else "standard"
         ix = LSHBloom(P, BANDS, ROWS, n_expected=nexp, fp_rate=fp, ngram=NGRAM,
-                      exec_mode=mode.split("/")[0], device=local,
-                      bloom_layout="blocked" if mode.endswith("/blocked") else "standard")
+                      exec_mode=mode.split("/")[0], device=local, bloom_layout=layout)
+        st0 = ix.stats()
+        index_bytes[layout] = st0["filter_bytes"] * st0["bands"]
 
         def step():
             ix.reset()
@@ -425,11 +428,19 @@ def run_ours(args):
         "stage_ms_per_step": {m: {"signature": v["sig_ms"] / args.steps,
                                   "bloom": v["bloom_ms"] / args.steps} for m, v in stage.items()},
         "roofline_probe": _probe_roofline(stage.get("plain")),
-        "blocked_layout": ({"batched_docs_per_s": results["batched/blocked"]["docs_per_s"],
-                            "plain_docs_per_s": results["plain/blocked"]["docs_per_s"],
-                            "dups_per_step": results["batched/blocked"]["dups_per_step"],
-                            "roofline_probe": _probe_roofline(stage["plain/blocked"])}
-                           if args.blocked else None),
+        "index_variants": ({lay: {"batched_docs_per_s": results[f"batched/{lay}"]["docs_per_s"],
+                                  "plain_docs_per_s": results[f"plain/{lay}"]["docs_per_s"],
+                                  "dups_per_step": results[f"batched/{lay}"]["dups_per_step"],
+                                  "index_bytes": index_bytes[lay],
+                                  "bloom_stage_ms_per_step":
+                                      stage[f"batched/{lay}"]["bloom_ms"] / args.steps,
+                                  "roofline_probe": _probe_roofline(stage[f"plain/{lay}"])}
+                            for lay in ("blocked", "exact")} | {
+                               "standard": {"index_bytes": index_bytes["standard"],
+                                            "dups_per_step": b["dups_per_step"],
+                                            "bloom_stage_ms_per_step":
+                                                stage["batched"]["bloom_ms"] / args.steps}}
+                           if args.variants else None),
         "serve": serve,
         "item_shingles": item_shingles,
         "cpu_baseline": cpu,
@@ -452,8 +463,8 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-serve", action="store_true")
-    ap.add_argument("--blocked", action="store_true",
-                    help="also measure the 256-bit blocked filter layout (both forms)")
+    ap.add_argument("--variants", action="store_true",
+                    help="also measure the blocked filter layout and the exact band-key index")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

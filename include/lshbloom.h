@@ -82,7 +82,17 @@ typedef enum { LSHB_INSERT_NONDUP = 0, LSHB_INSERT_ALL = 1 } lshb_insert_mode;
  * independent byte of a SplitMix64 word of y (y as for the standard layout),
  * block = high64(x * m/256); one 32-byte sector per probed key instead of k,
  * at a higher false-positive rate for the same m and k. */
-typedef enum { LSHB_BLOOM_STANDARD = 0, LSHB_BLOOM_BLOCKED = 1 } lshb_bloom_layout;
+/* EXACT_KEYS replaces the filters by exact sets of band keys (one
+ * open-addressing table of uint64 per band, 2^ceil(log2(2 n_expected)) slots,
+ * empty = 2^64-1): the bucket rule of MinHashLSH (Sec. 2.3) on the same band
+ * keys, i.e. the index without Bloom false positives (Eq. 3 with p_eff = 0),
+ * at several times the memory.  It is the same-device baseline for what the
+ * filters save; filter_bytes then returns the band's table. */
+typedef enum {
+    LSHB_BLOOM_STANDARD = 0,
+    LSHB_BLOOM_BLOCKED = 1,
+    LSHB_EXACT_KEYS = 2
+} lshb_bloom_layout;
 
 typedef enum {
     LSHB_EXEC_PLAIN = 0,   /* one kernel per stage */

@@ -323,7 +323,9 @@ OR_API void or_optimal_br(double T, uint32_t P, uint32_t *b_out, uint32_t *r_out
 
 typedef struct {
     uint32_t P, bands, rows, ngram, k, insert_all;
-    uint32_t layout;     /* 0: standard filter (Sec. 2.4), 1: 256-bit blocked variant */
+    uint32_t layout;     /* 0: standard filter (Sec. 2.4), 1: 256-bit blocked variant,
+                            2: exact band-key sets */
+    void *sets;          /* layout 2: one or_keyset per band */
     uint64_t m;          /* bits per filter */
     uint64_t words;      /* 64-bit words per filter */
     uint64_t *a, *b;     /* permutation coefficients */
@@ -353,11 +355,77 @@ OR_API or_index *or_index_create(uint32_t P, uint32_t bands, uint32_t rows, uint
     return ix;
 }
 
-/* Select the probe layout of an empty index (0 standard, 1 blocked). */
+/* Exact band-key sets (layout 2): the bucket rule of MinHashLSH (Sec. 2.3)
+ * applied to band keys, i.e. the index without Bloom false positives.  One
+ * open-addressing set per band, doubled when half full. */
+typedef struct {
+    uint64_t *slot; /* ~0 = empty (band keys are sums of r 32-bit values < 2^58) */
+    uint64_t cap, used;
+} or_keyset;
+
+static uint64_t or_set_home(uint64_t key, uint64_t cap) { return or_mix64(key) & (cap - 1); }
+
+static int or_set_contains(const or_keyset *s, uint64_t key) {
+    for (uint64_t i = or_set_home(key, s->cap);; i = (i + 1) & (s->cap - 1)) {
+        if (s->slot[i] == key) return 1;
+        if (s->slot[i] == ~0ull) return 0;
+    }
+}
+
+static void or_set_add(or_keyset *s, uint64_t key);
+
+static void or_set_grow(or_keyset *s) {
+    or_keyset t;
+    t.cap = s->cap * 2;
+    t.used = 0;
+    t.slot = (uint64_t *)malloc(sizeof(uint64_t) * t.cap);
+    memset(t.slot, 0xff, sizeof(uint64_t) * t.cap);
+    for (uint64_t i = 0; i < s->cap; ++i)
+        if (s->slot[i] != ~0ull) or_set_add(&t, s->slot[i]);
+    free(s->slot);
+    *s = t;
+}
+
+static void or_set_add(or_keyset *s, uint64_t key) {
+    if (2 * (s->used + 1) > s->cap) or_set_grow(s);
+    for (uint64_t i = or_set_home(key, s->cap);; i = (i + 1) & (s->cap - 1)) {
+        if (s->slot[i] == key) return;
+        if (s->slot[i] == ~0ull) {
+            s->slot[i] = key;
+            s->used++;
+            return;
+        }
+    }
+}
+
+/* Select the layout of an empty index: 0 standard filter, 1 blocked filter,
+ * 2 exact band-key sets. */
 OR_API int or_index_set_layout(or_index *ix, uint32_t layout) {
-    if (layout > 1 || (layout == 1 && ix->m % 256 != 0)) return -1;
+    if (layout > 2 || (layout == 1 && ix->m % 256 != 0)) return -1;
     ix->layout = layout;
+    if (layout == 2 && !ix->sets) {
+        ix->sets = calloc(ix->bands, sizeof(or_keyset));
+        or_keyset *s = (or_keyset *)ix->sets;
+        for (uint32_t j = 0; j < ix->bands; ++j) {
+            s[j].cap = 1024;
+            s[j].slot = (uint64_t *)malloc(sizeof(uint64_t) * 1024);
+            memset(s[j].slot, 0xff, sizeof(uint64_t) * 1024);
+        }
+    }
     return 0;
+}
+
+/* Keys of band j of an exact index (unordered); returns how many. */
+OR_API uint64_t or_index_exact_keys(const or_index *ix, uint32_t j, uint64_t *out, uint64_t cap) {
+    if (ix->layout != 2) return 0;
+    const or_keyset *s = (const or_keyset *)ix->sets + j;
+    uint64_t n = 0;
+    for (uint64_t i = 0; i < s->cap; ++i)
+        if (s->slot[i] != ~0ull) {
+            if (n < cap) out[n] = s->slot[i];
+            n++;
+        }
+    return n;
 }
 
 static void or_index_positions(const or_index *ix, uint64_t key, uint32_t j, uint64_t *q) {
@@ -367,6 +435,11 @@ static void or_index_positions(const or_index *ix, uint64_t key, uint32_t j, uin
 
 OR_API void or_index_destroy(or_index *ix) {
     if (!ix) return;
+    if (ix->sets) {
+        or_keyset *s = (or_keyset *)ix->sets;
+        for (uint32_t j = 0; j < ix->bands; ++j) free(s[j].slot);
+        free(ix->sets);
+    }
     free(ix->a); free(ix->b); free(ix->filt); free(ix);
 }
 
@@ -399,6 +472,16 @@ OR_API void or_index_dedup(or_index *ix, const uint64_t *offsets, const uint32_t
         or_signature(tokens + offsets[i], L, ix->ngram, ix->P, ix->a, ix->b, sig);
         or_band_keys(sig, ix->bands, ix->rows, keys);
         int dup = 0;
+        if (ix->layout == 2) {
+            or_keyset *sets = (or_keyset *)ix->sets;
+            for (uint32_t j = 0; j < ix->bands; ++j)
+                if (or_set_contains(&sets[j], keys[j])) dup = 1;
+            flags[i] = (uint8_t)dup;
+            if (ix->insert_all || !dup)
+                for (uint32_t j = 0; j < ix->bands; ++j) or_set_add(&sets[j], keys[j]);
+            ix->docs_seen++;
+            continue;
+        }
         for (uint32_t j = 0; j < ix->bands; ++j) {
             uint64_t *qj = q + (uint64_t)j * ix->k;
             or_index_positions(ix, keys[j], j, qj);

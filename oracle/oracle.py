@@ -60,6 +60,7 @@ def lib():
                 "or_probe_positions_blocked": (None, [C.c_uint64, C.c_uint32, C.c_uint64,
                                                       C.c_uint32, u64p]),
                 "or_index_set_layout": (C.c_int, [C.c_void_p, C.c_uint32]),
+                "or_index_exact_keys": (C.c_uint64, [C.c_void_p, C.c_uint32, u64p, C.c_uint64]),
                 "or_p_from_effective": (C.c_double, [C.c_double, C.c_uint32]),
                 "or_effective_from_p": (C.c_double, [C.c_double, C.c_uint32]),
                 "or_sizing": (None, [C.c_uint64, C.c_double, u64p, C.POINTER(C.c_uint32)]),
@@ -303,6 +304,13 @@ class OracleIndex:
         out = np.zeros((self.m + 7) // 8, np.uint8)
         lib().or_index_filter_bytes(self._h, j, _p(out, C.c_uint8))
         return out
+
+    def exact_keys(self, j: int) -> np.ndarray:
+        """Sorted band keys of band j (exact-set layout)."""
+        n = int(lib().or_index_exact_keys(self._h, j, None, 0))
+        out = np.zeros(max(n, 1), np.uint64)
+        lib().or_index_exact_keys(self._h, j, _p(out, C.c_uint64), n)
+        return np.sort(out[:n])
 
     def popcount(self, j: int) -> int:
         return int(lib().or_index_popcount(self._h, j))

@@ -79,7 +79,7 @@ class LSHBloom:
         cfg.device = device
         cfg.max_batch_docs, cfg.max_batch_tokens = max_batch_docs, max_batch_tokens
         cfg.item_shingles = item_shingles
-        cfg.bloom_layout = {"standard": 0, "blocked": 1}[bloom_layout]
+        cfg.bloom_layout = {"standard": 0, "blocked": 1, "exact": 2}[bloom_layout]
         keep = []
         if perm_a is not None:
             pa = np.ascontiguousarray(perm_a, np.uint64)
@@ -198,7 +198,8 @@ class LSHBloom:
     def _dims(self):
         if not hasattr(self, "_dim_cache"):
             s = self.stats()
-            self._dim_cache = (s["num_perm"], s["bands"], s["rows"], s["m_bits"], s["k"])
+            self._dim_cache = (s["num_perm"], s["bands"], s["rows"], s["m_bits"], s["k"],
+                               s["filter_bytes"])
         return self._dim_cache
 
     @property
@@ -229,7 +230,9 @@ class LSHBloom:
         return a, b
 
     def filter_bytes(self, band: int) -> np.ndarray:
-        out = np.zeros((self.m + 7) // 8, np.uint8)
+        """Filter `band` as bytes (bit q at byte q/8, LSB first); for the
+        exact-key layout, the band's table of uint64 slots."""
+        out = np.zeros(self._dims()[5], np.uint8)
         check(lib().lshbloom_filter_bytes(self._h, band, out.ctypes.data))
         return out
 

@@ -37,7 +37,7 @@ struct DynParams {
 
 struct BatchArgs {
     DynParams *dyn;
-    uint32_t item_shingles, ngram, P, npc, bands, rows, k, sketch_log2, blocked;
+    uint32_t item_shingles, ngram, P, npc, bands, rows, k, sketch_log2, layout;
     uint64_t m_bits, words_per_filter;
     const uint32_t *filters;
     uint32_t *item_count;      // D
@@ -217,7 +217,8 @@ __global__ void __launch_bounds__(kBatchThreads) k_batched(const __grid_constant
             for (uint32_t t = 0; t < A.rows; ++t) key += sigbuf[j * A.rows + t];
             A.keys[d * A.bands + j] = key;
             A.miss[d * A.bands + j] =
-                probe_band(A.filters + (uint64_t)j * A.words_per_filter, key, j, A.k, A.m_bits, A.blocked,
+                probe_band(A.filters + (uint64_t)j * A.words_per_filter, A.words_per_filter, key, j, A.k,
+                           A.m_bits, A.layout,
                            A.sketch1, A.sketch2, A.sketch_log2);
         }
         __syncwarp();
@@ -327,7 +328,7 @@ static BatchArgs make_args(lshbloom *h, BatchedState *b) {
     a.bands = h->bands;
     a.rows = h->rows;
     a.k = h->k;
-    a.blocked = h->blocked ? 1u : 0u;
+    a.layout = h->layout;
     a.m_bits = h->m;
     a.words_per_filter = h->words_per_filter;
     a.filters = h->filters;

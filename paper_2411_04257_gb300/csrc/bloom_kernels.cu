@@ -33,13 +33,13 @@ __global__ void k_probe_mark(const __grid_constant__ BloomArgs A) {
          idx += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t j = (uint32_t)(idx % A.bands);
         const uint32_t *F = A.filters + (uint64_t)j * A.words_per_filter;
-        if (A.k <= 24) {
-            const ProbeSeq ps(A.keys[idx], j, A.m_bits, A.blocked);
+        if (A.k <= 24 && A.layout != 2) {
+            const ProbeSeq ps(A.keys[idx], j, A.m_bits, A.layout);
             A.miss[idx] = probe_band_unrolled<24>(F, ps, j, A.k, A.m_bits, A.sketch1, A.sketch2,
                                                   A.sketch_bits_log2);
         } else {
-            A.miss[idx] = probe_band(F, A.keys[idx], j, A.k, A.m_bits, A.blocked, A.sketch1, A.sketch2,
-                                     A.sketch_bits_log2);
+            A.miss[idx] = probe_band(F, A.words_per_filter, A.keys[idx], j, A.k, A.m_bits, A.layout,
+                                     A.sketch1, A.sketch2, A.sketch_bits_log2);
         }
     }
 }
@@ -59,7 +59,7 @@ __global__ void k_classify(const __grid_constant__ BloomArgs A) {
             A.prehit[d] = 1;
             continue;
         }
-        const ProbeSeq ps(A.keys[idx], j, A.m_bits, A.blocked);
+        const ProbeSeq ps(A.keys[idx], j, A.m_bits, A.layout);
         bool all = true;
         uint64_t mm = miss;
         while (mm && all) {
@@ -194,7 +194,7 @@ __global__ void k_rk_insert(const __grid_constant__ BloomArgs A, const uint32_t 
         const uint64_t d = ulist[idx / A.bands];
         const uint32_t j = (uint32_t)(idx % A.bands);
         if (!((A.cand[d] >> j) & 1ull)) continue;
-        const ProbeSeq ps(A.keys[d * A.bands + j], j, A.m_bits, A.blocked);
+        const ProbeSeq ps(A.keys[d * A.bands + j], j, A.m_bits, A.layout);
         uint64_t mm = A.miss[d * A.bands + j];
         while (mm) {
             const uint32_t u = __ffsll((long long)mm) - 1;
@@ -217,7 +217,7 @@ __global__ void k_fixed_setters(const __grid_constant__ BloomArgs A, ResolveTabl
         const uint32_t j = (uint32_t)(idx % A.bands);
         uint64_t mm = A.miss[idx];
         if (!mm) continue;
-        const ProbeSeq ps(A.keys[idx], j, A.m_bits, A.blocked);
+        const ProbeSeq ps(A.keys[idx], j, A.m_bits, A.layout);
         while (mm) {
             const uint32_t u = __ffsll((long long)mm) - 1;
             mm &= mm - 1;
@@ -237,7 +237,7 @@ __global__ void k_cache_slots(const __grid_constant__ BloomArgs A, const uint32_
         const uint64_t d = ulist[idx / A.bands];
         const uint32_t j = (uint32_t)(idx % A.bands);
         const uint64_t miss = A.miss[d * A.bands + j];
-        const ProbeSeq ps(A.keys[d * A.bands + j], j, A.m_bits, A.blocked);
+        const ProbeSeq ps(A.keys[d * A.bands + j], j, A.m_bits, A.layout);
         uint32_t *out = T.slots + idx * A.k;
         for (uint32_t u = 0; u < A.k; ++u) {
             uint32_t s = kNone;
@@ -348,8 +348,13 @@ __global__ void k_insert(const __grid_constant__ BloomArgs A, const uint8_t *ins
         uint64_t mm = A.miss[idx];
         if (!mm) continue;
         const uint32_t j = (uint32_t)(idx % A.bands);
-        const ProbeSeq ps(A.keys[idx], j, A.m_bits, A.blocked);
         uint32_t *F = A.filters + (uint64_t)j * A.words_per_filter;
+        if (A.layout == 2) {
+            if (!exact_insert(reinterpret_cast<uint64_t *>(F), A.words_per_filter / 2, A.keys[idx]))
+                atomicOr(A.error, kErrTableFull);
+            continue;
+        }
+        const ProbeSeq ps(A.keys[idx], j, A.m_bits, A.layout);
         while (mm) {
             const uint32_t u = __ffsll((long long)mm) - 1;
             mm &= mm - 1;
@@ -386,6 +391,22 @@ static int grid_for(uint64_t n, int threads) {
 cudaError_t launch_popcount(const uint32_t *words, uint64_t n, unsigned long long *out,
                             cudaStream_t s) {
     k_popcount<<<grid_for(n, 256), 256, 0, s>>>(words, n, out); count_launch();
+    return cudaGetLastError();
+}
+
+__global__ void k_count_occupied(const uint64_t *__restrict__ slots, uint64_t n,
+                                 unsigned long long *out) {
+    unsigned long long c = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        c += slots[i] != ~0ull;
+    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(LSHB_FULL_MASK, c, off);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+cudaError_t launch_count_occupied(const uint64_t *slots, uint64_t n, unsigned long long *out,
+                                  cudaStream_t s) {
+    k_count_occupied<<<grid_for(n, 256), 256, 0, s>>>(slots, n, out); count_launch();
     return cudaGetLastError();
 }
 

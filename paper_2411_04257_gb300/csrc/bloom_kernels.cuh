@@ -13,7 +13,7 @@ struct BloomArgs {
     uint64_t D;
     const uint64_t *D_dev;      // when set, the batch size is read from device memory
     uint32_t bands, k;
-    uint32_t blocked;           // 1: 256-bit blocked filter layout
+    uint32_t layout;            // 0 standard filter, 1 256-bit blocked filter, 2 exact key sets
     uint64_t m_bits, words_per_filter;
     uint32_t *filters;          // bands x words_per_filter
     const uint64_t *keys;       // D x bands
@@ -81,12 +81,52 @@ __device__ __forceinline__ uint64_t probe_band_unrolled(const uint32_t *F, const
     return miss;
 }
 
+// Exact-key layout: the band's table of uint64 keys (empty = ~0), linear
+// probing from mix64(key); the table is never more than half full.
+__device__ __forceinline__ bool exact_contains(const uint64_t *T, uint64_t cap, uint64_t key) {
+    uint64_t s = mix64(key) & (cap - 1);
+    for (uint64_t i = 0; i < cap; ++i) {
+        const uint64_t v = __ldg(T + s);
+        if (v == key) return true;
+        if (v == ~0ull) return false;
+        s = (s + 1) & (cap - 1);
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool exact_insert(uint64_t *T, uint64_t cap, uint64_t key) {
+    uint64_t s = mix64(key) & (cap - 1);
+    for (uint64_t i = 0; i < cap; ++i) {
+        const unsigned long long prev =
+            atomicCAS((unsigned long long *)(T + s), ~0ull, (unsigned long long)key);
+        if (prev == ~0ull || prev == key) return true;
+        s = (s + 1) & (cap - 1);
+    }
+    return false;
+}
+
+// Sketch mark of one missing position (first mark sketch1, later ones sketch2).
+__device__ __forceinline__ void sketch_mark(uint64_t g, uint32_t *sk1, uint32_t *sk2,
+                                            uint32_t sk_log2) {
+    const uint64_t si = sketch_index(g, sk_log2);
+    const uint32_t bit = 1u << (si & 31);
+    const uint32_t old = atomicOr(sk1 + (si >> 5), bit);
+    if (old & bit) atomicOr(sk2 + (si >> 5), bit);
+}
+
 // Compact form (few registers): loads in groups of 8, atomics one by one.
 // Used where the probe is a small phase of a register-heavy kernel.
-__device__ __forceinline__ uint64_t probe_band(const uint32_t *F, uint64_t key, uint32_t j,
-                                               uint32_t k, uint64_t m, bool blocked, uint32_t *sk1,
-                                               uint32_t *sk2, uint32_t sk_log2) {
-    const ProbeSeq ps(key, j, m, blocked);
+// words_per_filter (uint32 words) sizes the exact-key table: words/2 slots.
+__device__ __forceinline__ uint64_t probe_band(const uint32_t *F, uint64_t words_per_filter,
+                                               uint64_t key, uint32_t j, uint32_t k, uint64_t m,
+                                               uint32_t layout, uint32_t *sk1, uint32_t *sk2,
+                                               uint32_t sk_log2) {
+    if (layout == 2) {
+        if (exact_contains(reinterpret_cast<const uint64_t *>(F), words_per_filter / 2, key)) return 0;
+        sketch_mark((uint64_t)j * m + key, sk1, sk2, sk_log2);
+        return 1;
+    }
+    const ProbeSeq ps(key, j, m, layout);
     uint64_t miss = 0;
     for (uint32_t u0 = 0; u0 < k; u0 += 8) {
         uint64_t q[8];
@@ -128,5 +168,7 @@ cudaError_t launch_finalize_insert(const BloomArgs &a, const uint32_t *ulist, ui
                                    uint8_t *insd, unsigned long long *dup_count, cudaStream_t s);
 cudaError_t launch_popcount(const uint32_t *words, uint64_t n, unsigned long long *out,
                             cudaStream_t s);
+cudaError_t launch_count_occupied(const uint64_t *slots, uint64_t n, unsigned long long *out,
+                                  cudaStream_t s);
 
 }  // namespace lshb

@@ -137,15 +137,26 @@ __device__ __forceinline__ uint32_t perm_lo32(uint32_t h, uint32_t a0, uint32_t 
 // Kirsch-Mitzenmacher double hashing over the m bits.  Blocked layout (the
 // variant beyond the paper): one 256-bit block per key, each position an
 // independent byte of a SplitMix64 word.
+// The exact-key layout has a single "position" per band: the key itself.
+constexpr uint64_t kExactTag = ~1ull;
+
 struct ProbeSeq {
-    uint64_t x, y, m, base;  // base: first bit of the key's block, ~0 for the standard layout
-    __device__ __forceinline__ ProbeSeq(uint64_t key, uint32_t band, uint64_t m_bits, bool blocked) {
+    uint64_t x, y, m, base;  // base: first bit of the key's block, ~0 standard, kExactTag exact
+    __device__ __forceinline__ ProbeSeq(uint64_t key, uint32_t band, uint64_t m_bits,
+                                        uint32_t layout) {
+        m = m_bits;
+        if (layout == 2) {
+            x = key;
+            y = 0;
+            base = kExactTag;
+            return;
+        }
         x = mix64(key ^ ((uint64_t)band * kGolden));
         y = mix64(x ^ kProbeSalt) | 1ull;
-        m = m_bits;
-        base = blocked ? (__umul64hi(x, m_bits >> 8) << 8) : ~0ull;
+        base = layout == 1 ? (__umul64hi(x, m_bits >> 8) << 8) : ~0ull;
     }
     __device__ __forceinline__ uint64_t pos(uint32_t u) const {
+        if (base == kExactTag) return x;
         if (base != ~0ull) {
             const uint64_t w = mix64(y + (uint64_t)(u >> 3) * kGolden);
             return base + ((w >> (8 * (u & 7))) & 255);

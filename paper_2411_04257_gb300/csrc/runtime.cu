@@ -145,7 +145,7 @@ static lshb_status validate_config(const lshb_config *c) {
     if (!(c->fp_rate > 0.0 && c->fp_rate < 1.0)) return fail(LSHB_ERR_ARG, "fp_rate must be in (0,1)");
     if (c->insert_mode > 1) return fail(LSHB_ERR_ARG, "bad insert_mode");
     if (c->exec_mode > 1) return fail(LSHB_ERR_ARG, "bad exec_mode");
-    if (c->bloom_layout > 1) return fail(LSHB_ERR_ARG, "bad bloom_layout");
+    if (c->bloom_layout > 2) return fail(LSHB_ERR_ARG, "bad bloom_layout");
     if (c->item_shingles != 0 && (c->item_shingles < 64 || c->item_shingles > (1u << 20)))
         return fail(LSHB_ERR_ARG, "item_shingles must be 0 (autotuned) or 64..2^20");
     if ((c->perm_a == nullptr) != (c->perm_b == nullptr))
@@ -201,12 +201,22 @@ lshb_status lshb::init_handle(lshbloom *h, const lshb_config *cfg) {
     h->ngram = cfg->ngram;
     h->insert_all = cfg->insert_mode == LSHB_INSERT_ALL;
     h->blocked = cfg->bloom_layout == LSHB_BLOOM_BLOCKED;
+    h->layout = cfg->bloom_layout;
     h->p = cfg->fp_is_effective ? 1.0 - std::pow(1.0 - cfg->fp_rate, 1.0 / (double)cfg->bands)
                                 : cfg->fp_rate;
     if (!(h->p > 0.0 && h->p < 1.0)) return fail(LSHB_ERR_ARG, "per-filter rate out of range");
     size_filter(cfg->n_expected, h->p, &h->m, &h->k);
     if (h->k > (uint32_t)kMaxK) return fail(LSHB_ERR_ARG, "k = %u exceeds 64; raise fp_rate", h->k);
     h->words_per_filter = ((h->m / 32) + 31) / 32 * 32;  // 128-byte aligned filters
+    if (h->layout == LSHB_EXACT_KEYS) {
+        // One table of uint64 keys per band, at most half full at n_expected;
+        // the key itself is the one "position" (global id band * 2^58 + key).
+        uint64_t cap = 1024;
+        while (cap < 2 * cfg->n_expected) cap <<= 1;
+        h->k = 1;
+        h->m = 1ull << 58;
+        h->words_per_filter = cap * 2;
+    }
     h->a.resize(h->P);
     h->b.resize(h->P);
     if (cfg->perm_a) {
@@ -242,7 +252,7 @@ lshb_status lshb::init_handle(lshbloom *h, const lshb_config *cfg) {
         h->filters = nullptr;
         return fail(LSHB_ERR_OOM, "filters: %zu bytes", fbytes);
     }
-    CK(cudaMemsetAsync(h->filters, 0, fbytes, h->stream));
+    CK(cudaMemsetAsync(h->filters, h->layout == LSHB_EXACT_KEYS ? 0xff : 0, fbytes, h->stream));
     CK(cudaMalloc(&h->counters, 256));
     CK(cudaMemsetAsync(h->counters, 0, 256, h->stream));
     CK(cudaMallocHost(&h->host_counters, 256));
@@ -446,7 +456,7 @@ BloomArgs lshb::bloom_args(lshbloom *h, uint64_t D) {
     b.D = D;
     b.bands = h->bands;
     b.k = h->k;
-    b.blocked = h->blocked ? 1u : 0u;
+    b.layout = h->layout;
     b.m_bits = h->m;
     b.words_per_filter = h->words_per_filter;
     b.filters = h->filters;
@@ -481,7 +491,7 @@ lshb_status lshb::run_bloom(lshbloom *h, uint64_t D, uint8_t *flags_dev, cudaStr
     h->probe_pending = true;
     // distinct 32-byte sectors the probes address: k per band key, or one
     // (the key's block) in the blocked layout
-    h->probe_sectors += D * h->bands * (h->blocked ? 1u : h->k);
+    h->probe_sectors += D * h->bands * (h->layout == LSHB_BLOOM_STANDARD ? h->k : 1u);
     uint32_t *ulist = (uint32_t *)h->buf(B_ULIST).ptr;
     CK(launch_classify(A, (uint32_t *)h->buf(B_BLOCKCNT).ptr, h->counters + C_NU, ulist, s));
     CK(cudaMemcpyAsync(h->host_counters, h->counters, 64, cudaMemcpyDeviceToHost, s));
@@ -743,7 +753,9 @@ extern "C" lshb_status lshbloom_filter_bytes(lshbloom_t *h, uint32_t band, uint8
     std::lock_guard<std::mutex> lock(h->mu);
     CK(cudaSetDevice(h->device));
     const uint8_t *src = (const uint8_t *)(h->filters + (uint64_t)band * h->words_per_filter);
-    CK(cudaMemcpyAsync(host_out, src, (h->m + 7) / 8, cudaMemcpyDeviceToHost, h->stream));
+    const size_t nbytes =
+        h->layout == LSHB_EXACT_KEYS ? (size_t)h->words_per_filter * 4 : (size_t)(h->m + 7) / 8;
+    CK(cudaMemcpyAsync(host_out, src, nbytes, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return LSHB_OK;
 }
@@ -752,7 +764,8 @@ extern "C" lshb_status lshbloom_reset(lshbloom_t *h) {
     if (!h) return fail(LSHB_ERR_ARG, "NULL handle");
     std::lock_guard<std::mutex> lock(h->mu);
     CK(cudaSetDevice(h->device));
-    CK(cudaMemsetAsync(h->filters, 0, (size_t)h->bands * h->words_per_filter * 4, h->stream));
+    CK(cudaMemsetAsync(h->filters, h->layout == LSHB_EXACT_KEYS ? 0xff : 0,
+                       (size_t)h->bands * h->words_per_filter * 4, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     h->docs_seen = h->dups_seen = h->resolve_rounds = h->uncertain_docs = 0;
     return LSHB_OK;
@@ -772,7 +785,7 @@ extern "C" lshb_status lshbloom_stats(lshbloom_t *h, lshb_stats *out) {
     out->exec_mode = h->cfg.exec_mode;
     out->item_shingles = h->item_shingles;
     out->m_bits = h->m;
-    out->filter_bytes = h->m / 8;
+    out->filter_bytes = h->layout == LSHB_EXACT_KEYS ? h->words_per_filter * 4 : h->m / 8;
     out->docs_seen = h->docs_seen;
     out->dups_seen = h->dups_seen;
     out->fp_rate = h->p;
@@ -785,13 +798,19 @@ extern "C" lshb_status lshbloom_stats(lshbloom_t *h, lshb_stats *out) {
     out->probe_ms = h->t_probe_ms;
     out->probe_sectors = h->probe_sectors;
     unsigned long long *cnt = (unsigned long long *)(h->counters + C_POPCOUNT);
+    const bool exact = h->layout == LSHB_EXACT_KEYS;
     for (uint32_t j = 0; j < h->bands; ++j) {
         CK(cudaMemsetAsync(cnt, 0, 8, h->stream));
-        CK(launch_popcount(h->filters + (uint64_t)j * h->words_per_filter, h->words_per_filter, cnt,
-                           h->stream));
+        const uint32_t *f = h->filters + (uint64_t)j * h->words_per_filter;
+        if (exact)
+            CK(launch_count_occupied((const uint64_t *)f, h->words_per_filter / 2, cnt, h->stream));
+        else
+            CK(launch_popcount(f, h->words_per_filter, cnt, h->stream));
         CK(cudaMemcpyAsync(h->host_counters, h->counters, 64, cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
-        out->fill[j] = (double)*(unsigned long long *)(h->host_counters + C_POPCOUNT) / (double)h->m;
+        // set bits per bit, or occupied slots per slot for the exact-key tables
+        out->fill[j] = (double)*(unsigned long long *)(h->host_counters + C_POPCOUNT) /
+                       (exact ? (double)(h->words_per_filter / 2) : (double)h->m);
     }
     return LSHB_OK;
 }

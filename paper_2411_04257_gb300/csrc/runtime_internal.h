@@ -63,6 +63,7 @@ struct lshbloom {
     uint32_t P = 0, bands = 0, rows = 0, ngram = 0, k = 0;
     bool insert_all = false;
     bool blocked = false;  // 256-bit blocked filter layout
+    uint32_t layout = 0;   // 0 standard, 1 blocked, 2 exact key sets
     double p = 0.0;
     uint64_t m = 0, words_per_filter = 0;
     std::vector<uint64_t> a, b;

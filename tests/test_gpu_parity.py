@@ -204,6 +204,25 @@ def test_blocked_layout(lshb, oracle, corpus, exec_mode, tmp_path):
         assert np.array_equal(fb, ref.filter_bytes(j))
 
 
+@pytest.mark.parametrize("exec_mode", ["batched", "plain"])
+def test_exact_key_index(lshb, oracle, corpus, exec_mode):
+    """Exact band-key sets (the MinHashLSH bucket rule on band keys) against the
+    oracle's exact mode: flags, and every band's key set."""
+    off, tok = _small_corpus(corpus, n=1800, dup_frac=0.4)
+    ix = lshb.LSHBloom(121, 11, 11, n_expected=1800, bloom_layout="exact", exec_mode=exec_mode,
+                       max_batch_docs=800)
+    ref = oracle.OracleIndex(121, 11, 11, n_expected=1800, layout=2)
+    got = np.concatenate([ix.dedup(*_dev(off[:901], tok)).cpu().numpy(),
+                          ix.dedup(*_dev(off[900:], tok)).cpu().numpy()])
+    want = ref.dedup(off, tok)
+    assert np.array_equal(got, want)
+    for j in range(11):
+        table = ix.filter_bytes(j).view(np.uint64)
+        assert np.array_equal(np.sort(table[table != np.uint64(2**64 - 1)]), ref.exact_keys(j))
+    st = ix.stats()
+    assert st["k"] == 1 and st["filter_bytes"] == 4096 * 8
+
+
 @pytest.mark.parametrize("ngram", [1, 7])
 def test_dedup_other_ngrams(lshb, oracle, corpus, ngram):
     off, tok = _small_corpus(corpus, n=800)

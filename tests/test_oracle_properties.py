@@ -243,6 +243,34 @@ def test_blocked_false_positive_closed_form(oracle, fp):
     assert rate > 1.5 * std                       # blocking costs accuracy at equal m
 
 
+def test_exact_key_sets_equal_a_set_replay(oracle):
+    """Layout 2 (exact band-key sets, the MinHashLSH bucket rule on band keys)
+    equals a replay with Python sets; the Bloom index flags a superset (no
+    false negatives) and the difference is its false positives."""
+    from synth import corpus
+    spec = corpus.CorpusSpec(n_docs=2500, seed=6, length_median=100, length_min=0,
+                             length_max=600, dup_frac=0.35, dup_lo=0.0, dup_hi=0.1)
+    off, toks = corpus.generate(spec)
+    ex = oracle.OracleIndex(121, 11, 11, n_expected=2500, fp_rate=1e-3, layout=2)
+    bl = oracle.OracleIndex(121, 11, 11, n_expected=2500, fp_rate=1e-3)
+    fe, fb = ex.dedup(off, toks), bl.dedup(off, toks)
+    sigs = oracle.batch_signatures(off, toks, 5, ex.a, ex.b)
+    keys = sigs[:, :121].astype(np.uint64).reshape(-1, 11, 11).sum(axis=2)
+    sets = [set() for _ in range(11)]
+    want = np.zeros(len(fe), np.uint8)
+    for i in range(len(fe)):
+        want[i] = any(int(keys[i, j]) in sets[j] for j in range(11))
+        if not want[i]:
+            for j in range(11):
+                sets[j].add(int(keys[i, j]))
+    assert np.array_equal(fe, want)
+    # The Bloom index differs only by its false positives (which, not being
+    # inserted, can also unflag a later copy): the totals stay close.
+    assert abs(int(fb.sum()) - int(fe.sum())) <= 25
+    for j in (0, 5, 10):
+        assert ex.exact_keys(j).tolist() == sorted(sets[j])
+
+
 def test_blocked_stream_semantics(oracle):
     doc = np.arange(100, 400, dtype=np.uint32)
     off, toks = _csr([doc, doc, np.arange(5000, 5300, dtype=np.uint32)])
