@@ -48,7 +48,13 @@ __device__ __forceinline__ uint32_t perm_lo32w(uint32_t h, uint32_t a0, uint32_t
                                                uint64_t b1) {
     const uint64_t t = (uint64_t)a0 * h + b0;
     const uint64_t V = (uint64_t)a1 * h + b1 + (t >> 32);
+#if defined(LSHB_PERM_FUNNEL)
+    const uint32_t vlo = (uint32_t)V, vhi = (uint32_t)(V >> 32);
+    const uint32_t q = __funnelshift_r(vlo, vhi, 29);  // V >> 29 fits in 32 bits
+    const uint64_t s = (((uint64_t)(vlo & 0x1fffffffu) << 32) | (uint32_t)t) + q;
+#else
     const uint64_t s = (((V & 0x1fffffffull) << 32) | (uint32_t)t) + (V >> 29);
+#endif
     return (uint32_t)s - 1u + (uint32_t)(s >> 61);
 }
 
