@@ -41,20 +41,18 @@ struct LaneCoef {
 // 2^61 = 1 (mod p) folds it to s = (V mod 2^29) 2^32 + (t mod 2^32) + (V >> 29),
 // 1 <= s < 2^61 + 2^32, s = x + 1 (mod p).  Then x mod p = s - 1 - p [s >= 2^61],
 // whose low 32 bits are s_lo - 1 + (s >> 61) since 2^61 = 0 (mod 2^32).
-// Two wide multiplies and ALU work; written in C, the compiler's split between
-// the IMAD and ALU pipes measured faster than hand-placing the 64-bit adds and
-// shifts on the IMAD pipe (the wide multiplies already load it).
+// Two wide multiplies and ALU work.  V < 2^61, so V >> 29 fits in 32 bits and
+// is taken with one funnel shift of V's two halves instead of a 64-bit shift
+// (4.6% faster signature kernel, measured); the rest is left to the compiler,
+// whose split between the IMAD and ALU pipes measured faster than
+// hand-placing the 64-bit adds on the IMAD pipe.
 __device__ __forceinline__ uint32_t perm_lo32w(uint32_t h, uint32_t a0, uint32_t a1, uint64_t b0,
                                                uint64_t b1) {
     const uint64_t t = (uint64_t)a0 * h + b0;
     const uint64_t V = (uint64_t)a1 * h + b1 + (t >> 32);
-#if defined(LSHB_PERM_FUNNEL)
     const uint32_t vlo = (uint32_t)V, vhi = (uint32_t)(V >> 32);
-    const uint32_t q = __funnelshift_r(vlo, vhi, 29);  // V >> 29 fits in 32 bits
+    const uint32_t q = __funnelshift_r(vlo, vhi, 29);  // V >> 29
     const uint64_t s = (((uint64_t)(vlo & 0x1fffffffu) << 32) | (uint32_t)t) + q;
-#else
-    const uint64_t s = (((V & 0x1fffffffull) << 32) | (uint32_t)t) + (V >> 29);
-#endif
     return (uint32_t)s - 1u + (uint32_t)(s >> 61);
 }
 
