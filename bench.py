@@ -18,6 +18,7 @@ the same workload.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -43,6 +44,43 @@ SM_MAX_MHZ = 2070.0
 IMAD_PER_PERMHASH = 4       # two 32x32->64 products (lo and hi halves) per (a*h + b)
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per document of
+# the two roofline kernels, from one ncu capture on the 100k-document
+# peS2o-shaped batch (same corpus, same 11 x 116.8 MB filters); a launch's
+# traffic scales with the documents it processes (65,536- and 100,000-document
+# launches agree within 0.5% per document).  Reported only while the kernel's
+# sources hash to the captured state: a changed kernel reports null.
+_CSRC = "paper_2411_04257_gb300/csrc/"
+_TRAFFIC = {
+    "k_batched": {"bytes_per_doc": 54788.0,
+                  "sources": ["batched.cu", "sig_kernels.cuh", "lshb_device.cuh",
+                              "bloom_kernels.cuh", "lshb_internal.h"],
+                  "sha256": "42a708ccffd1d84914021653083af26ecd28be023d6940c754c1362d0fc05700",
+                  "profile": "profiles/dram_traffic_pes2o100k.md"},
+    "k_probe_mark": {"bytes_per_doc": 25543.0,
+                     "sources": ["bloom_kernels.cu", "bloom_kernels.cuh", "lshb_device.cuh",
+                                 "lshb_internal.h"],
+                     "sha256": "d5bf0690d64adc08892eadc500fea049d5067b3ffe7fc51d38ca651c2ed86e69",
+                     "profile": "profiles/dram_traffic_pes2o100k.md"},
+}
+
+
+def _sources_sha256(files):
+    h = hashlib.sha256()
+    for rel in files:
+        with open(os.path.join(ROOT, _CSRC, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def _traffic(kernel, docs_per_launch):
+    """Measured DRAM bytes of one launch of `kernel`, or None once it changed."""
+    t = _TRAFFIC[kernel]
+    if not docs_per_launch or _sources_sha256(t["sources"]) != t["sha256"]:
+        return None
+    return t["bytes_per_doc"] * docs_per_launch
+
+
 def _measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -52,16 +90,21 @@ def _measured_peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
-def _probe_roofline(st):
+def _probe_roofline(st, standard_layout=True):
     """The stand-alone probe kernel of the plain form: each probe of a band key
-    reads one 32-byte sector of a filter that does not fit in L2."""
+    reads one 32-byte sector of a filter that does not fit in L2.  One probe
+    launch per chunk; `traffic` is known for the standard layout only."""
     if not st or not st["probe_ms"] or not st["probe_sectors"]:
         return None
     peaks, src = _measured_peaks()
     gbs = st["probe_sectors"] * 32 / (st["probe_ms"] / 1e3) / 1e9
+    docs_per_launch = st["docs"] / max(1, st["sig_chunks"])
+    traffic = _traffic("k_probe_mark", docs_per_launch) if standard_layout else None
     return {"bound": "hbm", "kernel": "k_probe_mark (plain form)", "achieved": gbs,
             "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
-            "traffic": None, "peak_source": f"hbm_gbs, {src}",
+            "traffic": traffic, "algorithmic_bytes_per_launch":
+                st["probe_sectors"] * 32 / max(1, st["sig_chunks"]),
+            "peak_source": f"hbm_gbs, {src}",
             "algorithmic_bytes": "32 B per addressed sector: b*k = 187 per document "
                                  "(standard layout), b = 11 (blocked layout)"}
 
@@ -345,7 +388,8 @@ def run_ours(args):
                        "bloom_ms": s1["bloom_ms"] - s0["bloom_ms"],
                        "sig_chunks": s1["sig_chunks"] - s0["sig_chunks"],
                        "probe_ms": s1["probe_ms"] - s0["probe_ms"],
-                       "probe_sectors": s1["probe_sectors"] - s0["probe_sectors"]}
+                       "probe_sectors": s1["probe_sectors"] - s0["probe_sectors"],
+                       "docs": D * args.steps}
         dt, docs = reduce_over_ranks(dt, float(D * args.steps), dev)
         _, ph = reduce_over_ranks(dt, float(permhashes * args.steps), dev)
         ix.reset()
@@ -420,7 +464,8 @@ def run_ours(args):
         "gpu_launches": launches["batched"],
         "roofline": {"bound": "alu", "kernel": "signature (SHA-1 + MinHash + band keys)",
                      "achieved": achieved_imad / 1e12, "peak": peak_imad / 1e12,
-                     "unit": "T int-mul/s", "frac": achieved_imad / peak_imad, "traffic": None,
+                     "unit": "T int-mul/s", "frac": achieved_imad / peak_imad,
+                     "traffic": _traffic("k_batched", D * args.steps / max(1, sb["sig_chunks"])),
                      "launch_ms": 1e3 * sb["sig_ms"] / 1e3 / max(1, sb["sig_chunks"]),
                      "launches_per_step": sb["sig_chunks"] / args.steps,
                      "perm_hashes_per_s": permhashes / sig_s,
@@ -434,7 +479,7 @@ def run_ours(args):
                                   "index_bytes": index_bytes[lay],
                                   "bloom_stage_ms_per_step":
                                       stage[f"batched/{lay}"]["bloom_ms"] / args.steps,
-                                  "roofline_probe": _probe_roofline(stage[f"plain/{lay}"])}
+                                  "roofline_probe": _probe_roofline(stage[f"plain/{lay}"], False)}
                             for lay in ("blocked", "exact")} | {
                                "standard": {"index_bytes": index_bytes["standard"],
                                             "dups_per_step": b["dups_per_step"],
