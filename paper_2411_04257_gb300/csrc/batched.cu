@@ -188,8 +188,6 @@ __global__ void __launch_bounds__(kBatchThreads) k_batched(const __grid_constant
         const uint64_t s_begin = (it - ibeg) * A.item_shingles;
         const uint64_t s_end = min(S, s_begin + A.item_shingles);
         uint32_t mn[PPL];
-#pragma unroll
-        for (int t = 0; t < PPL; ++t) mn[t] = 0xffffffffu;
         fold_range<NG, PPL>(mn, cf, tk, L, n, s_begin, s_end, nullptr, hbuf, lane);
         if (icnt > 1) {
             uint32_t *row = A.sig_partial + d * A.P;

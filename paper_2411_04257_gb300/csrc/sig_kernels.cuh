@@ -6,7 +6,7 @@
 // shared-memory slot; then every lane folds all 32 hashes, read back as
 // broadcast 128-bit loads, into the PPL permutations it owns: lane l owns
 // permutations l, l+32, ..., with their coefficients in registers.  The inner
-// loop is ~12 integer instructions per (shingle, permutation), the loop body
+// loop is a few integer instructions per (shingle, permutation), the loop body
 // is small enough to stay in the instruction cache, and no cross-lane
 // reduction is needed at the end of a document.
 #pragma once
@@ -56,15 +56,41 @@ __device__ __forceinline__ uint32_t perm_lo32w(uint32_t h, uint32_t a0, uint32_t
     return (uint32_t)s - 1u + (uint32_t)(s >> 61);
 }
 
-template <int PPL>
-__device__ __forceinline__ void fold4(uint32_t (&mn)[PPL], const LaneCoef<PPL> &c, uint4 hv) {
+// Fast form of perm_lo32w: s_lo - 1 without the (s >> 61) term.  That term is
+// nonzero only when s >= 2^61, and s = (V mod 2^29) 2^32 + (t mod 2^32) +
+// (V >> 29) with V >> 29 < 2^32 reaches 2^61 only if V mod 2^29 = 2^29 - 1
+// (probability 2^-29 per value).  `guard` keeps the minimum of
+// ((~V) mod 2^29) << 3 = -8 V - 8 (mod 2^32), which is zero exactly for such
+// a V: a range whose guard stays nonzero has every value exact, and one whose
+// guard reaches zero is recomputed with perm_lo32w.  This saves the mask,
+// the 64-bit add and the final shift-and-add of the exact form on the ALU
+// pipe, which bounds the kernel, for one multiply-add on the FMA pipe.
+__device__ __forceinline__ uint32_t perm_lo32_fast(uint32_t h, uint32_t a0, uint32_t a1,
+                                                   uint64_t b0, uint64_t b1, uint32_t &guard) {
+    const uint64_t t = (uint64_t)a0 * h + b0;
+    const uint64_t V = (uint64_t)a1 * h + b1 + (t >> 32);
+    const uint32_t vlo = (uint32_t)V, vhi = (uint32_t)(V >> 32);
+    guard = min(guard, vlo * 0xfffffff8u + 0xfffffff8u);
+    return (uint32_t)t + __funnelshift_r(vlo, vhi, 29) - 1u;
+}
+
+template <int PPL, bool FAST>
+__device__ __forceinline__ void fold4(uint32_t (&mn)[PPL], const LaneCoef<PPL> &c, uint4 hv,
+                                      uint32_t &guard) {
 #pragma unroll
     for (int t = 0; t < PPL; ++t) {
         uint32_t m = mn[t];
-        m = min(m, perm_lo32w(hv.x, c.a0[t], c.a1[t], c.b0[t], c.b1[t]));
-        m = min(m, perm_lo32w(hv.y, c.a0[t], c.a1[t], c.b0[t], c.b1[t]));
-        m = min(m, perm_lo32w(hv.z, c.a0[t], c.a1[t], c.b0[t], c.b1[t]));
-        m = min(m, perm_lo32w(hv.w, c.a0[t], c.a1[t], c.b0[t], c.b1[t]));
+        if constexpr (FAST) {
+            m = min(m, perm_lo32_fast(hv.x, c.a0[t], c.a1[t], c.b0[t], c.b1[t], guard));
+            m = min(m, perm_lo32_fast(hv.y, c.a0[t], c.a1[t], c.b0[t], c.b1[t], guard));
+            m = min(m, perm_lo32_fast(hv.z, c.a0[t], c.a1[t], c.b0[t], c.b1[t], guard));
+            m = min(m, perm_lo32_fast(hv.w, c.a0[t], c.a1[t], c.b0[t], c.b1[t], guard));
+        } else {
+            m = min(m, perm_lo32w(hv.x, c.a0[t], c.a1[t], c.b0[t], c.b1[t]));
+            m = min(m, perm_lo32w(hv.y, c.a0[t], c.a1[t], c.b0[t], c.b1[t]));
+            m = min(m, perm_lo32w(hv.z, c.a0[t], c.a1[t], c.b0[t], c.b1[t]));
+            m = min(m, perm_lo32w(hv.w, c.a0[t], c.a1[t], c.b0[t], c.b1[t]));
+        }
         mn[t] = m;
     }
 }
@@ -107,18 +133,19 @@ __device__ __forceinline__ uint64_t shingle_count(uint64_t L, uint32_t n) {
 // Fold shingles [s_begin, s_end) of one document into the lane's minima.
 // hbuf is the warp's 32-entry, 16-byte aligned shared slot.  When `hashes` is
 // given the shingle hashes are read from it (plain form) instead of computed.
-template <int NG, int PPL>
-__device__ __forceinline__ void fold_range(uint32_t (&mn)[PPL], const LaneCoef<PPL> &cf,
-                                           const uint32_t *tk, uint64_t L, uint32_t n,
-                                           uint64_t s_begin, uint64_t s_end,
-                                           const uint32_t *hashes, uint32_t *hbuf, int lane) {
+template <int NG, int PPL, bool FAST>
+__device__ __forceinline__ void fold_pass(uint32_t (&mn)[PPL], const LaneCoef<PPL> &cf,
+                                          const uint32_t *tk, uint64_t L, uint32_t n,
+                                          uint64_t s_begin, uint64_t s_end,
+                                          const uint32_t *hashes, uint32_t *hbuf, int lane,
+                                          uint32_t &guard) {
     const uint64_t S = shingle_count(L, n);
     if (L < n) {
         // one short shingle of all L tokens (only when the range covers it)
         if (s_begin == 0 && s_end > 0 && L > 0) {
             uint32_t h = hashes ? __ldg(hashes) : bswap32(sha1_h0_tokens(tk, (uint32_t)L));
             const uint4 hv = make_uint4(h, h, h, h);
-            fold4<PPL>(mn, cf, hv);
+            fold4<PPL, false>(mn, cf, hv, guard);
         }
         return;
     }
@@ -139,8 +166,40 @@ __device__ __forceinline__ void fold_range(uint32_t (&mn)[PPL], const LaneCoef<P
         __syncwarp();
         const uint4 *hv4 = reinterpret_cast<const uint4 *>(hbuf);
         const uint32_t groups = (cnt + 3) >> 2;
-        for (uint32_t g = 0; g < groups; ++g) fold4<PPL>(mn, cf, hv4[g]);
+        for (uint32_t g = 0; g < groups; ++g) fold4<PPL, FAST>(mn, cf, hv4[g], guard);
     }
+}
+
+// The exact pass, kept out of line: inlined next to the fast pass it raised
+// the persistent kernel from 95 to 122 registers (8 instead of 10 blocks per
+// SM) and cost 17% of its throughput; called, it costs a stack frame on a
+// path taken about once per 2^29 / (shingles x permutations) ranges.
+template <int NG, int PPL>
+__device__ __noinline__ void fold_exact(uint32_t (&mn)[PPL], const LaneCoef<PPL> &cf,
+                                        const uint32_t *tk, uint64_t L, uint32_t n,
+                                        uint64_t s_begin, uint64_t s_end,
+                                        const uint32_t *hashes, uint32_t *hbuf, int lane) {
+    uint32_t guard = 0xffffffffu;
+#pragma unroll
+    for (int t = 0; t < PPL; ++t) mn[t] = 0xffffffffu;
+    fold_pass<NG, PPL, false>(mn, cf, tk, L, n, s_begin, s_end, hashes, hbuf, lane, guard);
+}
+
+// The lane's minima over shingles [s_begin, s_end) (all-ones when the range
+// is empty): the fast pass, and, in the rare case that its guard tripped in
+// some lane, the whole range again in exact arithmetic.  Called by all 32
+// lanes of the warp with the same range.
+template <int NG, int PPL>
+__device__ __forceinline__ void fold_range(uint32_t (&mn)[PPL], const LaneCoef<PPL> &cf,
+                                           const uint32_t *tk, uint64_t L, uint32_t n,
+                                           uint64_t s_begin, uint64_t s_end,
+                                           const uint32_t *hashes, uint32_t *hbuf, int lane) {
+    uint32_t guard = 0xffffffffu;
+#pragma unroll
+    for (int t = 0; t < PPL; ++t) mn[t] = 0xffffffffu;
+    fold_pass<NG, PPL, true>(mn, cf, tk, L, n, s_begin, s_end, hashes, hbuf, lane, guard);
+    if (__any_sync(LSHB_FULL_MASK, guard == 0u))
+        fold_exact<NG, PPL>(mn, cf, tk, L, n, s_begin, s_end, hashes, hbuf, lane);
 }
 
 // Write the pass minima (sig_out) and, for a single full pass, band keys.
@@ -191,8 +250,6 @@ __global__ void __launch_bounds__(kSigThreads) k_sig(const __grid_constant__ Sig
         const uint32_t *tk = A.tokens + (o0 - A.tok_base);
         const uint32_t *hs = A.hashes ? A.hashes + (o0 - A.tok_base) : nullptr;
         uint32_t mn[PPL];
-#pragma unroll
-        for (int t = 0; t < PPL; ++t) mn[t] = 0xffffffffu;
         fold_range<NG, PPL>(mn, cf, tk, L, n, 0, shingle_count(L, n), hs, hbuf, lane);
         sig_epilogue<PPL>(A, d, mn, sm.sig[wib], lane);
     }

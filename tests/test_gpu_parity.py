@@ -73,6 +73,59 @@ def test_signatures(lshb, oracle, corpus, P, ngram):
     assert bad.size == 0, f"signature rows differ: {bad[:10]}"
 
 
+MERSENNE = (1 << 61) - 1
+
+
+def _residue_coefficients(oracle, off, tok, P, seed):
+    """Coefficients under which, for every permutation i, one chosen shingle
+    of one chosen document lands on a residue tau < 2^32 (mostly 0-3):
+    b_i = (tau - a_i h) mod p.  With a_i >= 2^40 the integer a h + b is many
+    times p, so the Mersenne fold of a h + b + 1 lands at or above 2^61, the
+    case whose final conditional subtraction is rarest (probability ~2^-29 on
+    random data).  Returns (a, b, which documents, fraction in that case)."""
+    hashes, counts = oracle.batch_shingle_hashes(off, tok, 5)
+    starts = np.concatenate([[0], np.cumsum(counts.astype(np.int64))])
+    rnd = np.random.default_rng(seed)
+    docs = [d for d in range(len(counts)) if counts[d] > 0]
+    a = np.zeros(P, np.uint64)
+    b = np.zeros(P, np.uint64)
+    hit_docs, in_case = [], 0
+    for i in range(P):
+        d = int(docs[rnd.integers(len(docs))])
+        h = int(hashes[starts[d] + rnd.integers(int(counts[d]))])
+        ai = int(rnd.integers(1 << 40, MERSENNE - 1))
+        tau = int(rnd.choice([0, 1, 2, 3, int(rnd.integers(0, 1 << 32))]))
+        bi = (tau - ai * h) % MERSENNE
+        a[i], b[i] = ai, bi
+        y = ai * h + bi + 1
+        in_case += ((y & MERSENNE) + (y >> 61)) >= (1 << 61)
+        hit_docs.append(d)
+    return a, b, sorted(set(hit_docs)), in_case / P
+
+
+@pytest.mark.parametrize("P", [121, 64, 256])
+def test_signatures_at_constructed_residues(lshb, oracle, corpus, P):
+    """Both signature kernels (per document, and the batched form with
+    64-shingle items, so the residues fall in split documents too) on
+    coefficients that put shingles on residues 0-3 through the rare branch
+    of the modular reduction.  Compared with the oracle's exact arithmetic."""
+    off, tok = _small_corpus(corpus, n=300, seed=21, length_median=400, length_max=6000)
+    a, b, hit, frac = _residue_coefficients(oracle, off, tok, P, seed=P)
+    assert frac > 0.6                                # the test reaches the case
+    want = oracle.batch_signatures(off, tok, 5, a, b)
+    rows = 8 if P >= 88 else 4
+    ix = lshb.LSHBloom(P, 11, rows, perm_a=a, perm_b=b)
+    got = ix.signatures(*_dev(off, tok)).cpu().numpy().view(np.uint32)
+    bad = np.nonzero((got != want).any(axis=1))[0]
+    assert bad.size == 0, f"signature rows differ: {bad[:10]}"
+    assert (want[hit] <= 3).any()
+    keys_want = want[:, :11 * rows].astype(np.uint64).reshape(-1, 11, rows).sum(axis=2)
+    ixb = lshb.LSHBloom(P, 11, rows, perm_a=a, perm_b=b, exec_mode="batched", item_shingles=64,
+                        n_expected=1000)
+    _, keys = ixb.dedup_keys(*_dev(off, tok))
+    assert np.array_equal(keys.cpu().numpy().view(np.uint64), keys_want)
+
+
 @pytest.mark.parametrize("exec_mode", ["batched", "plain"])
 def test_band_keys(lshb, oracle, corpus, exec_mode):
     off, tok = _small_corpus(corpus, n=500)
