@@ -45,18 +45,18 @@ IMAD_PER_PERMHASH = 4       # two 32x32->64 products (lo and hi halves) per (a*h
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per document of
-# the two roofline kernels, from one ncu capture on the 100k-document
+# the two roofline kernels, from ncu captures on the 100k-document
 # peS2o-shaped batch (same corpus, same 11 x 116.8 MB filters); a launch's
 # traffic scales with the documents it processes (65,536- and 100,000-document
 # launches agree within 0.5% per document).  Reported only while the kernel's
 # sources hash to the captured state: a changed kernel reports null.
 _CSRC = "paper_2411_04257_gb300/csrc/"
 _TRAFFIC = {
-    "k_batched": {"bytes_per_doc": 54788.0,
+    "k_batched": {"bytes_per_doc": 55250.0,
                   "sources": ["batched.cu", "sig_kernels.cuh", "lshb_device.cuh",
                               "bloom_kernels.cuh", "lshb_internal.h"],
-                  "sha256": "42a708ccffd1d84914021653083af26ecd28be023d6940c754c1362d0fc05700",
-                  "profile": "profiles/dram_traffic_pes2o100k.md"},
+                  "sha256": "671010493a5054cdafb60be8ef60879efdf639e473541030b20f1418718dc44f",
+                  "profile": "profiles/k_batched_pes2o100k_ncu.md"},
     "k_probe_mark": {"bytes_per_doc": 25543.0,
                      "sources": ["bloom_kernels.cu", "bloom_kernels.cuh", "lshb_device.cuh",
                                  "lshb_internal.h"],
@@ -107,6 +107,24 @@ def _probe_roofline(st, standard_layout=True):
             "peak_source": f"hbm_gbs, {src}",
             "algorithmic_bytes": "32 B per addressed sector: b*k = 187 per document "
                                  "(standard layout), b = 11 (blocked layout)"}
+
+
+def _h2d_probe(h_src, d_dst, nbytes=4 << 30):
+    """Best of three pinned host->device copies of up to 4 GB, in GB/s."""
+    import torch
+    n = min(h_src.numel(), d_dst.numel(), nbytes // h_src.element_size())
+    if n == 0:
+        return None
+    st = torch.cuda.current_stream()
+    best = 0.0
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        d_dst[:n].copy_(h_src[:n], non_blocking=True)
+        e1.record(st)
+        e1.synchronize()
+        best = max(best, n * h_src.element_size() / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    return best
 
 
 def reduce_over_ranks(seconds: float, units: float, device=None):
@@ -419,17 +437,29 @@ def run_ours(args):
         for _ in range(max(1, args.warmup)):
             ixe.reset()
             ixe.dedup(h_off, h_tok, out=h_flags)
+        h2d_gbs = _h2d_probe(h_tok, tok)
         barrier_sync()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            ixe.reset()
-            ixe.dedup(h_off, h_tok, out=h_flags)
-        barrier_sync()
-        et = time.perf_counter() - t0
+        s0 = ixe.stats()
+        with Clocks(local) as ck:
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                ixe.reset()
+                ixe.dedup(h_off, h_tok, out=h_flags)
+            barrier_sync()
+            et = time.perf_counter() - t0
+        s1 = ixe.stats()
         et, docs = reduce_over_ranks(et, float(D * args.steps), dev)
         ixe.close()
         e2e = {"value": docs / et, "unit": "docs/s",
-               "h2d_bytes_per_step": (D + 1) * 8 + T * 4, "d2h_bytes_per_step": D}
+               "h2d_bytes_per_step": (D + 1) * 8 + T * 4, "d2h_bytes_per_step": D,
+               # context for the number: the pinned-copy bandwidth of this host
+               # just before the timed steps, the library's own kernel time of
+               # the steps (copies overlap it), and the clocks meanwhile
+               "h2d_probe_gbs": h2d_gbs,
+               "kernel_ms_per_step": (s1["sig_ms"] + s1["bloom_ms"] - s0["sig_ms"] - s0["bloom_ms"])
+                                     / args.steps,
+               "chunks_per_step": (s1["sig_chunks"] - s0["sig_chunks"]) / args.steps,
+               "clocks": ck.summary()}
         del h_tok
 
     serve = None
