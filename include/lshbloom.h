@@ -81,7 +81,9 @@ typedef enum { LSHB_INSERT_NONDUP = 0, LSHB_INSERT_ALL = 1 } lshb_insert_mode;
  * Singler 2007): all k positions of a key inside one 256-bit block, each an
  * independent byte of a SplitMix64 word of y (y as for the standard layout),
  * block = high64(x * m/256); one 32-byte sector per probed key instead of k,
- * at a higher false-positive rate for the same m and k. */
+ * at a higher false-positive rate for the same m and k.  A BLOCKED index is
+ * therefore sized by its own rule (lshbloom_filter_sizing): the fewest
+ * 256-bit blocks, over k, whose modelled rate meets the per-filter p. */
 /* EXACT_KEYS replaces the filters by exact sets of band keys (one
  * open-addressing table of uint64 per band, 2^ceil(log2(2 n_expected)) slots,
  * empty = 2^64-1): the bucket rule of MinHashLSH (Sec. 2.3) on the same band
@@ -248,6 +250,20 @@ LSHB_API lshb_status lshbloom_load(const char *path, int32_t device, lshbloom_t 
 /* (b, r) with b*r <= P minimising the equal-weight sum of the LSH false
  * positive and false negative integrals at threshold T (Eqs. 1-2, Sec. 4.3). */
 LSHB_API lshb_status lshbloom_optimal_br(double T, uint32_t P, uint32_t *b_out, uint32_t *r_out);
+
+/* Bits m and probe count k of one filter for n_expected keys at per-filter
+ * false-positive rate fp_rate, as lshbloom_create_ex sizes them.  STANDARD
+ * (and EXACT_KEYS' nominal figure): m = -n ln p / (ln 2)^2 (Sec. 4.5),
+ * rounded up to whole bits and a multiple of 256, k = max(1, round(m/n ln 2)).
+ * BLOCKED (beyond the paper): the smallest m, in 256-bit blocks, and its k
+ * (1 .. min(64, standard k + 8)) whose rate under the blocked model is at
+ * most p; the model takes Poisson(256 n / m) keys per block and, given i
+ * keys, the chance E[(Z/256)^k] that a query's k uniform positions all land
+ * on the Z bits that i*k uniform positions set.  Host only: no GPU needed.
+ * m_bits, k: caller-owned outputs.  LSHB_ERR_ARG for n_expected < 1, p
+ * outside (0, 1), an unknown layout or a NULL output. */
+LSHB_API lshb_status lshbloom_filter_sizing(uint64_t n_expected, double fp_rate, uint32_t layout,
+                                            uint64_t *m_bits, uint32_t *k);
 
 /* ---- Serving: continuous batching over resident indexes ----------------------
  *

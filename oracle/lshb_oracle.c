@@ -255,6 +255,136 @@ OR_API void or_sizing(uint64_t n, double p, uint64_t *m_bits, uint32_t *k) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Blocked layout (a design beyond the paper): every key's k positions lie   */
+/* in one 256-bit block, drawn uniformly with replacement inside it.  Its    */
+/* false-positive model and the sizing that meets a target rate with it.     */
+/* ------------------------------------------------------------------------ */
+
+/* One occupancy step: after one more uniform draw over 256 cells, the count
+ * of occupied cells moves from z-1 to z with probability (256-(z-1))/256 and
+ * stays at z with probability z/256. */
+static void or_occupancy_step(double *P) {
+    for (int z = 256; z >= 1; --z) P[z] = P[z] * z / 256.0 + P[z - 1] * (257 - z) / 256.0;
+    P[0] = 0.0;
+}
+
+typedef struct {
+    uint32_t k;
+    double occ[257];   /* law of the set-bit count after len * k draws */
+    double hit[257];   /* P(query all set | z set bits) */
+    double *g;         /* g[i] = P(query all set | i keys in the block) */
+    uint32_t len, cap;
+} or_blocked_model;
+
+static void or_blocked_model_init(or_blocked_model *M, uint32_t k) {
+    double q[257];
+    memset(q, 0, sizeof(q));
+    q[0] = 1.0;
+    for (uint32_t u = 0; u < k; ++u) or_occupancy_step(q);   /* distinct cells of a query */
+    for (int z = 0; z <= 256; ++z) {
+        double s = 0.0;
+        for (int d = 1; d <= 256 && d <= (int)k; ++d) {
+            if (q[d] == 0.0) continue;
+            double r = 1.0;                                   /* C(z, d) / C(256, d) */
+            for (int j = 0; j < d; ++j) r *= (double)(z - j) / (double)(256 - j);
+            if (z < d) r = 0.0;
+            s += q[d] * r;
+        }
+        M->hit[z] = s;
+    }
+    memset(M->occ, 0, sizeof(M->occ));
+    M->occ[0] = 1.0;
+    M->k = k;
+    M->g = NULL;
+    M->len = M->cap = 0;
+}
+
+static double or_blocked_model_g(or_blocked_model *M, uint32_t i) {
+    while (M->len <= i) {
+        if (M->len == M->cap) {
+            M->cap = M->cap ? 2 * M->cap : 256;
+            M->g = (double *)realloc(M->g, sizeof(double) * M->cap);
+        }
+        double s = 0.0;
+        for (int z = 0; z <= 256; ++z) s += M->occ[z] * M->hit[z];
+        M->g[M->len++] = s;
+        for (uint32_t u = 0; u < M->k; ++u) or_occupancy_step(M->occ);
+    }
+    return M->g[i];
+}
+
+/* Block loads Poisson(256 n / m); the rate is the load-weighted g. */
+static double or_blocked_model_fp(or_blocked_model *M, uint64_t n, uint64_t m) {
+    if (n == 0) return 0.0;
+    const double lam = 256.0 * (double)n / (double)m;
+    const double spread = 12.0 * sqrt(lam) + 30.0;
+    const double lo_r = floor(lam - spread), hi_r = ceil(lam + spread);
+    const uint32_t lo = lo_r < 0.0 ? 0u : (uint32_t)lo_r, hi = (uint32_t)hi_r;
+    double s = 0.0;
+    for (uint32_t i = lo; i <= hi; ++i) {
+        const double w = exp(-lam + (double)i * log(lam) - lgamma((double)i + 1.0));
+        s += w * or_blocked_model_g(M, i);
+    }
+    return s;
+}
+
+/* P(a query's k positions are all set | i keys in its block). */
+OR_API double or_blocked_hit(uint32_t i, uint32_t k) {
+    or_blocked_model M;
+    or_blocked_model_init(&M, k);
+    double g = or_blocked_model_g(&M, i);
+    free(M.g);
+    return g;
+}
+
+/* False-positive rate of one blocked filter of m bits holding n keys. */
+OR_API double or_fp_blocked(uint64_t n, uint64_t m, uint32_t k) {
+    or_blocked_model M;
+    or_blocked_model_init(&M, k);
+    double fp = or_blocked_model_fp(&M, n, m);
+    free(M.g);
+    return fp;
+}
+
+/* Sizing of the blocked layout: over k = 1 .. min(64, k_std + 8), the fewest
+ * 256-bit blocks whose model rate is at most p; the fewest blocks overall win
+ * (ties: the smaller k).  The rate falls as blocks are added, so each k is a
+ * bracket (from half the standard layout's blocks, doubling) and a bisection. */
+OR_API void or_sizing_blocked(uint64_t n, double p, uint64_t *m_bits, uint32_t *k_out) {
+    uint64_t m0;
+    uint32_t k0;
+    or_sizing(n, p, &m0, &k0);
+    const uint64_t B0 = m0 / 256;
+    const uint32_t kmax = k0 + 8 > 64 ? 64 : k0 + 8;
+    uint64_t bestB = UINT64_MAX;
+    uint32_t bestk = k0;
+    for (uint32_t k = 1; k <= kmax; ++k) {
+        or_blocked_model M;
+        or_blocked_model_init(&M, k);
+        uint64_t lo = B0 / 2 ? B0 / 2 : 1, hi = B0 ? B0 : 1;
+        int ok = 1;
+        while (or_blocked_model_fp(&M, n, 256 * hi) > p) {
+            lo = hi;
+            hi *= 2;
+            if (hi > (B0 << 24)) { ok = 0; break; }
+        }
+        if (ok) {
+            while (lo > 1 && or_blocked_model_fp(&M, n, 256 * lo) <= p) { hi = lo; lo /= 2; }
+            if (or_blocked_model_fp(&M, n, 256 * lo) <= p) hi = lo;
+            while (hi - lo > 1) {
+                const uint64_t mid = lo + (hi - lo) / 2;
+                if (or_blocked_model_fp(&M, n, 256 * mid) <= p) hi = mid;
+                else lo = mid;
+            }
+            if (hi < bestB) { bestB = hi; bestk = k; }
+        }
+        free(M.g);
+    }
+    *m_bits = 256 * bestB;
+    *k_out = bestk;
+}
+
+/* ------------------------------------------------------------------------ */
 /* LSH error model, Eqs. 1-4 (Sec. 4.3), and the (b, r) choice of Sec. 4.3   */
 /* and Sec. 4.5 (minimise the two LSH error integrals over b*r <= P).        */
 /* ------------------------------------------------------------------------ */

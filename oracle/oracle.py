@@ -64,6 +64,10 @@ def lib():
                 "or_p_from_effective": (C.c_double, [C.c_double, C.c_uint32]),
                 "or_effective_from_p": (C.c_double, [C.c_double, C.c_uint32]),
                 "or_sizing": (None, [C.c_uint64, C.c_double, u64p, C.POINTER(C.c_uint32)]),
+                "or_sizing_blocked": (None, [C.c_uint64, C.c_double, u64p,
+                                             C.POINTER(C.c_uint32)]),
+                "or_fp_blocked": (C.c_double, [C.c_uint64, C.c_uint64, C.c_uint32]),
+                "or_blocked_hit": (C.c_double, [C.c_uint32, C.c_uint32]),
                 "or_fp_lsh": (C.c_double, [C.c_double, C.c_uint32, C.c_uint32]),
                 "or_fn_lsh": (C.c_double, [C.c_double, C.c_uint32, C.c_uint32]),
                 "or_fp_bloom": (C.c_double, [C.c_double, C.c_double, C.c_uint32, C.c_double]),
@@ -213,6 +217,22 @@ def sizing(n: int, p: float):
     return int(m.value), int(k.value)
 
 
+def sizing_blocked(n: int, p: float):
+    """(m, k) of the blocked layout: the fewest 256-bit blocks meeting p."""
+    m = C.c_uint64()
+    k = C.c_uint32()
+    lib().or_sizing_blocked(n, p, C.byref(m), C.byref(k))
+    return int(m.value), int(k.value)
+
+
+def fp_blocked(n: int, m: int, k: int) -> float:
+    return float(lib().or_fp_blocked(n, m, k))
+
+
+def blocked_hit(i: int, k: int) -> float:
+    return float(lib().or_blocked_hit(i, k))
+
+
 def fp_lsh(T, b, r):
     return float(lib().or_fp_lsh(T, b, r))
 
@@ -247,7 +267,7 @@ class OracleIndex:
                  m: int | None = None, k: int | None = None, a=None, b=None,
                  layout: int = 0):
         p = p_from_effective(fp_rate, bands) if fp_is_effective else fp_rate
-        mm, kk = sizing(n_expected, p)
+        mm, kk = sizing_blocked(n_expected, p) if layout == 1 else sizing(n_expected, p)
         self.m = int(m) if m is not None else mm
         self.k = int(k) if k is not None else kk
         if a is None or b is None:

@@ -14,7 +14,7 @@ import numpy as np
 from ._native import (EXEC_BATCHED, EXEC_PLAIN, INSERT_ALL, INSERT_NONDUP, Config,
                       LSHBloomError, Stats, check, lib)
 
-__all__ = ["LSHBloom", "LSHBloomServer", "LSHBloomError", "optimal_br", "lib", "EXEC_PLAIN",
+__all__ = ["LSHBloom", "LSHBloomServer", "LSHBloomError", "optimal_br", "filter_sizing", "lib", "EXEC_PLAIN",
            "EXEC_BATCHED"]
 
 
@@ -51,6 +51,9 @@ def _out(n_items, row, np_dtype, torch_dtype, like_cuda_tensor):
     return a.ctypes.data, a
 
 
+_LAYOUTS = {"standard": 0, "blocked": 1, "exact": 2}
+
+
 class LSHBloom:
     """b Bloom filters, one per LSH band, fed in stream order.
 
@@ -79,7 +82,7 @@ class LSHBloom:
         cfg.device = device
         cfg.max_batch_docs, cfg.max_batch_tokens = max_batch_docs, max_batch_tokens
         cfg.item_shingles = item_shingles
-        cfg.bloom_layout = {"standard": 0, "blocked": 1, "exact": 2}[bloom_layout]
+        cfg.bloom_layout = _LAYOUTS[bloom_layout]
         keep = []
         if perm_a is not None:
             pa = np.ascontiguousarray(perm_a, np.uint64)
@@ -305,6 +308,15 @@ class LSHBloomServer:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def filter_sizing(n_expected: int, fp_rate: float, bloom_layout: str = "standard"):
+    """(m bits, k) of one filter as an index of this layout sizes it."""
+    m = C.c_uint64()
+    k = C.c_uint32()
+    check(lib().lshbloom_filter_sizing(n_expected, fp_rate, _LAYOUTS[bloom_layout],
+                                       C.byref(m), C.byref(k)))
+    return int(m.value), int(k.value)
 
 
 def optimal_br(T: float, P: int):

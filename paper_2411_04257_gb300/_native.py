@@ -72,6 +72,8 @@ _SIGS = {
     "lshbloom_load": (C.c_int, [C.c_char_p, C.c_int32, C.POINTER(_VP)]),
     "lshbloom_optimal_br": (C.c_int, [C.c_double, C.c_uint32, C.POINTER(C.c_uint32),
                                       C.POINTER(C.c_uint32)]),
+    "lshbloom_filter_sizing": (C.c_int, [C.c_uint64, C.c_double, C.c_uint32,
+                                         C.POINTER(C.c_uint64), C.POINTER(C.c_uint32)]),
     "lshbloom_server_create": (C.c_int, [C.POINTER(_VP), C.c_uint32, C.c_uint64, C.c_uint32,
                                          C.POINTER(_VP)]),
     "lshbloom_server_submit": (C.c_int, [_VP, C.c_uint32, _VP, _VP, C.c_uint64, _VP,

@@ -63,6 +63,102 @@ static void size_filter(uint64_t n, double p, uint64_t *m, uint32_t *k) {
     *k = (uint32_t)(kk < 1 ? 1 : kk);
 }
 
+// Blocked layout (not in the paper): a key's k positions are uniform draws,
+// with replacement, inside one 256-bit block.  With i keys in a block its
+// set-bit count Z has the occupancy law of i*k draws over 256 cells, and a
+// query's k draws all land on set bits with probability E[(Z/256)^k];
+// block loads are Poisson with mean 256 n / m.
+namespace {
+struct BlockedFpModel {
+    uint32_t k;
+    std::vector<double> occ = std::vector<double>(257, 0.0);  // law of Z after g.size() keys
+    std::vector<double> pw = std::vector<double>(257, 0.0);   // (z/256)^k
+    std::vector<double> g;                                    // g[i] = E[(Z/256)^k | i keys]
+    explicit BlockedFpModel(uint32_t k_) : k(k_) {
+        occ[0] = 1.0;
+        for (int z = 0; z <= 256; ++z) pw[z] = std::pow(z / 256.0, (double)k);
+    }
+    double hit(uint32_t i) {
+        while (g.size() <= i) {
+            double s = 0.0;
+            for (int z = 0; z <= 256; ++z) s += occ[z] * pw[z];
+            g.push_back(s);
+            for (uint32_t u = 0; u < k; ++u) {  // one more draw: z -> z or z+1
+                for (int z = 256; z >= 1; --z) occ[z] = occ[z] * (z / 256.0) + occ[z - 1] * ((257 - z) / 256.0);
+                occ[0] = 0.0;
+            }
+        }
+        return g[i];
+    }
+    double fp(uint64_t n, uint64_t m) {
+        if (n == 0) return 0.0;
+        const double lam = 256.0 * (double)n / (double)m;
+        const double half = 12.0 * std::sqrt(lam) + 30.0;
+        const uint32_t i0 = lam - half > 0.0 ? (uint32_t)std::floor(lam - half) : 0u;
+        const uint32_t i1 = (uint32_t)std::ceil(lam + half);
+        double s = 0.0;
+        for (uint32_t i = i0; i <= i1; ++i)
+            s += std::exp(-lam + i * std::log(lam) - std::lgamma(i + 1.0)) * hit(i);
+        return s;
+    }
+};
+}  // namespace
+
+// Bits and k of a blocked filter meeting rate p at n keys: for each k up to
+// the standard k + 8 (at most 64), the fewest blocks whose model rate is <= p
+// (the rate falls as blocks are added: bracket from half the standard
+// layout's blocks, then bisect); the fewest blocks over all k win, ties to
+// the smaller k.
+static void size_filter_blocked(uint64_t n, double p, uint64_t *m, uint32_t *k) {
+    uint64_t m_std;
+    uint32_t k_std;
+    size_filter(n, p, &m_std, &k_std);
+    const uint64_t B0 = std::max<uint64_t>(m_std / 256, 1);
+    const uint32_t kmax = std::min<uint32_t>(k_std + 8, kMaxK);
+    uint64_t best = ~0ull;
+    uint32_t best_k = k_std;
+    for (uint32_t kk = 1; kk <= kmax; ++kk) {
+        BlockedFpModel M(kk);
+        auto ok = [&](uint64_t blocks) { return M.fp(n, 256 * blocks) <= p; };
+        uint64_t lo = std::max<uint64_t>(B0 / 2, 1), hi = B0;
+        bool found = true;
+        while (!ok(hi)) {
+            lo = hi;
+            hi *= 2;
+            if (hi > (B0 << 24)) {
+                found = false;
+                break;
+            }
+        }
+        if (!found) continue;
+        while (lo > 1 && ok(lo)) {
+            hi = lo;
+            lo /= 2;
+        }
+        if (ok(lo)) hi = lo;
+        while (hi - lo > 1) {
+            const uint64_t mid = lo + (hi - lo) / 2;
+            (ok(mid) ? hi : lo) = mid;
+        }
+        if (hi < best) {
+            best = hi;
+            best_k = kk;
+        }
+    }
+    *m = 256 * best;
+    *k = best_k;
+}
+
+extern "C" lshb_status lshbloom_filter_sizing(uint64_t n_expected, double fp_rate, uint32_t layout,
+                                              uint64_t *m_bits, uint32_t *k) {
+    if (!m_bits || !k || n_expected < 1 || !(fp_rate > 0.0 && fp_rate < 1.0) ||
+        layout > LSHB_EXACT_KEYS)
+        return fail(LSHB_ERR_ARG, "bad argument");
+    if (layout == LSHB_BLOOM_BLOCKED) size_filter_blocked(n_expected, fp_rate, m_bits, k);
+    else size_filter(n_expected, fp_rate, m_bits, k);
+    return LSHB_OK;
+}
+
 // SplitMix64 stream (Steele, Lea, Flood 2014) of `seed`: a_i, b_i alternately.
 static void draw_coefficients(uint64_t seed, uint32_t P, uint64_t *a, uint64_t *b) {
     uint64_t state = seed;
@@ -205,7 +301,8 @@ lshb_status lshb::init_handle(lshbloom *h, const lshb_config *cfg) {
     h->p = cfg->fp_is_effective ? 1.0 - std::pow(1.0 - cfg->fp_rate, 1.0 / (double)cfg->bands)
                                 : cfg->fp_rate;
     if (!(h->p > 0.0 && h->p < 1.0)) return fail(LSHB_ERR_ARG, "per-filter rate out of range");
-    size_filter(cfg->n_expected, h->p, &h->m, &h->k);
+    if (h->layout == LSHB_BLOOM_BLOCKED) size_filter_blocked(cfg->n_expected, h->p, &h->m, &h->k);
+    else size_filter(cfg->n_expected, h->p, &h->m, &h->k);
     if (h->k > (uint32_t)kMaxK) return fail(LSHB_ERR_ARG, "k = %u exceeds 64; raise fp_rate", h->k);
     h->words_per_filter = ((h->m / 32) + 31) / 32 * 32;  // 128-byte aligned filters
     if (h->layout == LSHB_EXACT_KEYS) {

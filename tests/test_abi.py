@@ -77,3 +77,17 @@ def test_struct_layouts_match_header(built):
     os.unlink(exe)
     assert vals == [ctypes.sizeof(_native.Config), ctypes.sizeof(_native.Stats),
                     _native.Config.exec_mode.offset, _native.Stats.fill.offset]
+
+
+def test_filter_sizing_matches_the_oracle(built, oracle):
+    """lshbloom_filter_sizing (host only) equals the oracle's sizing for both
+    Bloom layouts; the two implement the blocked model independently."""
+    import paper_2411_04257_gb300 as L
+    cases = [(39_000_000, 1e-5), (1_000_000, 1e-3), (1600, 1e-4), (100_000, 1e-5), (10_000, 0.3),
+             (5, 0.01), (1, 0.5), (123_457, 0.0123), (39_000_000, 1 - (1 - 1e-10) ** (1 / 42))]
+    for n, p in cases:
+        assert L.filter_sizing(n, p, "standard") == oracle.sizing(n, p)
+        assert L.filter_sizing(n, p, "blocked") == oracle.sizing_blocked(n, p)
+    for bad in ((0, 0.1), (10, 0.0), (10, 1.0)):
+        with pytest.raises(L.LSHBloomError):
+            L.filter_sizing(*bad)

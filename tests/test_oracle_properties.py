@@ -229,8 +229,13 @@ def test_blocked_positions_share_one_block(oracle):
 
 @pytest.mark.parametrize("fp", [1e-5, 1e-3])
 def test_blocked_false_positive_closed_form(oracle, fp):
+    """At the standard layout's m and k (explicitly given: a blocked index
+    otherwise sizes itself by its own rule), the blocked rate of the oracle's
+    index follows the model, the oracle's own model agrees with this one, and
+    both are above the standard rate."""
     n = 100_000
-    ix = oracle.OracleIndex(11, 11, 1, n_expected=n, fp_rate=fp, layout=1)
+    mm, kk = oracle.sizing(n, fp)
+    ix = oracle.OracleIndex(11, 11, 1, n_expected=n, fp_rate=fp, layout=1, m=mm, k=kk)
     rnd = np.random.default_rng(31)
     keys = rnd.integers(0, 2**63, size=n, dtype=np.uint64) * np.uint64(2) + np.uint64(1)
     ix.insert_keys(0, keys)
@@ -241,6 +246,72 @@ def test_blocked_false_positive_closed_form(oracle, fp):
     std = (1 - math.exp(-ix.k * n / ix.m)) ** ix.k
     assert abs(rate / want - 1) < 0.25, (rate, want)
     assert rate > 1.5 * std                       # blocking costs accuracy at equal m
+    assert oracle.fp_blocked(n, ix.m, ix.k) == pytest.approx(want, rel=1e-9)
+
+
+def test_blocked_model_reduces_to_the_standard_filter_at_k1(oracle):
+    """With one position per key the blocks are just cells of one flat
+    filter: the blocked rate is the standard 1 - exp(-n/m)."""
+    for n, m in ((1000, 256_000), (50_000, 256 * 1000), (7, 256), (10**6, 256 * 10**5)):
+        assert oracle.fp_blocked(n, m, 1) == pytest.approx(1 - math.exp(-n / m), rel=1e-12)
+
+
+def _stirling2(n, k):
+    row = [1] + [0] * k                           # S(0, j)
+    for i in range(1, n + 1):
+        new = [0] * (k + 1)
+        for j in range(1, min(i, k) + 1):
+            new[j] = j * row[j] + row[j - 1]
+        row = new
+    return row[k]
+
+
+def test_blocked_hit_matches_the_occupancy_formula(oracle):
+    """P(a query's k positions are all set | i keys in the block) =
+    E[(Z/256)^k], Z the occupied cells after i k uniform draws, with
+    P(Z = s) = C(256, s) s! S(ik, s) / 256^(ik) (Stirling numbers of the
+    second kind), summed in exact rationals."""
+    from fractions import Fraction
+    for i, k in ((0, 5), (1, 1), (1, 2), (1, 5), (2, 3), (3, 4), (6, 1), (4, 6)):
+        draws = i * k
+        want = Fraction(0)
+        for z in range(0, min(draws, 256) + 1):
+            pz = Fraction(math.comb(256, z) * math.factorial(z) * _stirling2(draws, z),
+                          256 ** draws)
+            want += pz * Fraction(z, 256) ** k
+        assert oracle.blocked_hit(i, k) == pytest.approx(float(want), rel=1e-11, abs=1e-300)
+
+
+def test_blocked_sizing_meets_its_target_on_fresh_keys(oracle):
+    """An index sized by the blocked rule for p = 1e-3 shows that rate on
+    3M keys it never saw (about 3,000 false positives: +-2% noise)."""
+    n, p = 100_000, 1e-3
+    m, k = oracle.sizing_blocked(n, p)
+    ix = oracle.OracleIndex(11, 11, 1, n_expected=n, fp_rate=p, layout=1)
+    assert (ix.m, ix.k) == (m, k)
+    rnd = np.random.default_rng(77)
+    keys = rnd.integers(0, 2**63, size=n, dtype=np.uint64) * np.uint64(2) + np.uint64(1)
+    ix.insert_keys(3, keys)
+    fresh = rnd.integers(0, 2**63, size=3_000_000, dtype=np.uint64) * np.uint64(2)
+    rate = float(ix.query_keys(3, fresh).mean())
+    model = oracle.fp_blocked(n, m, k)
+    assert model <= p
+    assert abs(rate / model - 1) < 0.1, (rate, model)
+
+
+@pytest.mark.parametrize("n,p", [(39_000_000, 1e-5), (1_000_000, 1e-3), (1600, 1e-4),
+                                 (10_000, 0.3), (5, 0.01)])
+def test_blocked_sizing_is_the_fewest_blocks(oracle, n, p):
+    """The blocked rule returns a whole number of blocks that meets p, one
+    block fewer meets it for no k in the searched range, and it never needs
+    fewer bits than the standard filter."""
+    m, k = oracle.sizing_blocked(n, p)
+    ms, ks = oracle.sizing(n, p)
+    assert m % 256 == 0 and m >= ms
+    assert oracle.fp_blocked(n, m, k) <= p
+    if m > 256:
+        for kk in range(1, min(64, ks + 8) + 1):
+            assert oracle.fp_blocked(n, m - 256, kk) > p
 
 
 def test_exact_key_sets_equal_a_set_replay(oracle):
