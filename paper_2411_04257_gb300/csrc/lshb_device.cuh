@@ -119,20 +119,6 @@ __device__ __forceinline__ uint32_t sha1_h0_tokens(const uint32_t *tok, uint32_t
 
 __device__ __forceinline__ uint32_t shingle_hash_from_h0(uint32_t h0) { return bswap32(h0); }
 
-// ((a*h + b) mod (2^61 - 1)) mod 2^32, exact, with a = a1:a0, b = b1:b0,
-// a, b < 2^61 - 1 (so a1, b1 < 2^29) and h < 2^32.
-//   t = a0*h + b0                < 2^64
-//   V = a1*h + b1 + (t >> 32)    < 2^61, and a*h + b = V*2^32 + (t mod 2^32)
-// 2^61 = 1 (mod p) folds the top: s = (V mod 2^29)*2^32 + (t mod 2^32) + (V >> 29),
-// s < 2p; the residue is s - p when s + 1 >= 2^61, and -p = +1 (mod 2^32).
-__device__ __forceinline__ uint32_t perm_lo32(uint32_t h, uint32_t a0, uint32_t a1, uint32_t b0,
-                                              uint32_t b1) {
-    const uint64_t t = (uint64_t)a0 * h + b0;
-    const uint64_t V = (uint64_t)a1 * h + b1 + (t >> 32);
-    const uint64_t s1 = ((((V & 0x1fffffffull) << 32) | (uint32_t)t) + (V >> 29)) + 1ull;
-    return (uint32_t)s1 - 1u + (uint32_t)(s1 >> 61);
-}
-
 // Probe sequence of one band key (library convention).  Standard layout:
 // Kirsch-Mitzenmacher double hashing over the m bits.  Blocked layout (the
 // variant beyond the paper): one 256-bit block per key, each position an
