@@ -116,7 +116,10 @@ typedef struct {
     uint32_t exec_mode;       /* lshb_exec_mode (default BATCHED) */
     int32_t device;           /* CUDA device ordinal, -1 = current */
     uint64_t max_batch_docs;  /* docs per internal chunk, 0 = default (262144) */
-    uint64_t max_batch_tokens;/* tokens per internal chunk, 0 = default (2^28) */
+    uint64_t max_batch_tokens;/* tokens per internal chunk, 0 = default (2^28 in the plain
+                                 form; 2^31 in the batched form, where host inputs
+                                 are staged through two device buffers of that size,
+                                 the first chunk of a call ramped up from 2^28) */
     uint32_t item_shingles;   /* batched mode: shingles per work item, 0 = autotuned */
     uint32_t bloom_layout;    /* lshb_bloom_layout (default STANDARD) */
     uint32_t reserved[6];

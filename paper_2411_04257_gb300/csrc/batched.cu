@@ -490,10 +490,14 @@ lshb_status run_batched(lshbloom *h, const uint64_t *offsets, const uint32_t *to
     const uint64_t dmax = h->max_docs_batched;
     std::vector<std::pair<uint64_t, uint64_t>> chunks;
     {
+        // Staged host inputs take the same large chunks as resident ones, so a
+        // batch costs a few host round trips, ramped from 2^28 tokens so that
+        // the first, unhidden copy stays short.
         const uint64_t save_docs = h->max_docs, save_tok = h->max_tokens;
         h->max_docs = dmax;
-        if (tok_dev) h->max_tokens = h->max_tokens_batched;
-        plan_chunks(h, off, true, chunks);
+        h->max_tokens = h->max_tokens_batched;
+        plan_chunks(h, off, true, chunks,
+                    tok_dev ? 0 : std::min<uint64_t>(1ull << 28, h->max_tokens_batched));
         h->max_docs = save_docs;
         h->max_tokens = save_tok;
     }

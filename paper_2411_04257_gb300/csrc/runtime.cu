@@ -435,15 +435,22 @@ lshb_status lshb::host_offsets(lshbloom *h, const uint64_t *offsets, uint64_t D,
 // Chunks [lo, hi) of at most max_docs documents and, when tokens are staged or
 // the plain path stores shingle hashes, at most max_tokens tokens (a longer
 // single document is a chunk of its own).
+// With first_tokens > 0 the token bound ramps up: first_tokens for the first
+// chunk, four times more for each next one, up to max_tokens (staged host
+// inputs: the first copy, which nothing hides, stays short, and each later
+// copy fits under the compute of the chunk before it).
 void lshb::plan_chunks(const lshbloom *h, const std::vector<uint64_t> &off, bool bound_tokens,
-                       std::vector<std::pair<uint64_t, uint64_t>> &chunks) {
+                       std::vector<std::pair<uint64_t, uint64_t>> &chunks, uint64_t first_tokens) {
     chunks.clear();
     const uint64_t D = off.size() - 1;
     uint64_t lo = 0;
+    uint64_t ramp = first_tokens;
     while (lo < D) {
         uint64_t hi = std::min(D, lo + h->max_docs);
         if (bound_tokens) {
-            const uint64_t lim = off[lo] + h->max_tokens;
+            const uint64_t cap = ramp ? std::min(ramp, h->max_tokens) : h->max_tokens;
+            if (ramp && ramp < h->max_tokens) ramp *= 4;
+            const uint64_t lim = off[lo] + cap;
             // largest hi with off[hi] <= lim, at least lo + 1
             uint64_t a = lo + 1, b = hi;
             if (off[a] > lim) {

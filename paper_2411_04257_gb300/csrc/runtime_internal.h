@@ -104,7 +104,8 @@ bool is_device_pointer(const void *p);
 lshb_status host_offsets(lshbloom *h, const uint64_t *offsets, uint64_t D, bool dev,
                          std::vector<uint64_t> &out);
 void plan_chunks(const lshbloom *h, const std::vector<uint64_t> &off, bool bound_tokens,
-                 std::vector<std::pair<uint64_t, uint64_t>> &chunks);
+                 std::vector<std::pair<uint64_t, uint64_t>> &chunks,
+                 uint64_t first_tokens = 0);
 lshb_status ensure_chunk_scratch(lshbloom *h, uint64_t Dc, uint64_t Tc, bool plain_hashes,
                                  bool need_sig);
 lshb_status ensure_stage(lshbloom *h, uint64_t Tc);
