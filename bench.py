@@ -459,6 +459,10 @@ def run_ours(args):
                "kernel_ms_per_step": (s1["sig_ms"] + s1["bloom_ms"] - s0["sig_ms"] - s0["bloom_ms"])
                                      / args.steps,
                "chunks_per_step": (s1["sig_chunks"] - s0["sig_chunks"]) / args.steps,
+               "h2d_ms_per_step": (s1["h2d_ms"] - s0["h2d_ms"]) / args.steps,
+               "h2d_gbs_in_steps": ((s1["h2d_bytes"] - s0["h2d_bytes"])
+                                    / max(1e-9, (s1["h2d_ms"] - s0["h2d_ms"]) / 1e3) / 1e9),
+               "call_ms_per_step": (s1["call_ms"] - s0["call_ms"]) / args.steps,
                "clocks": ck.summary()}
         del h_tok
 

@@ -142,6 +142,9 @@ typedef struct {
     double probe_ms;          /* device time of the stand-alone probe kernel (plain form) */
     uint64_t probe_sectors;   /* 32-byte sectors that kernel's probes address (k per band key,
                                  one per band key in the blocked layout) */
+    double h2d_ms;            /* copy-stream time of the token copies of host inputs (CUDA events) */
+    uint64_t h2d_bytes;       /* bytes those copies moved */
+    double call_ms;           /* host wall-clock time spent inside dedup calls */
 } lshb_stats;
 
 /* Fill *cfg with defaults: P=121, b=11, r=11, n=5, n_expected=10000,

@@ -37,6 +37,7 @@ class Stats(C.Structure):
         ("uncertain_docs", C.c_uint64), ("kernel_launches", C.c_uint64),
         ("sig_ms", C.c_double), ("bloom_ms", C.c_double), ("sig_chunks", C.c_uint64),
         ("probe_ms", C.c_double), ("probe_sectors", C.c_uint64),
+        ("h2d_ms", C.c_double), ("h2d_bytes", C.c_uint64), ("call_ms", C.c_double),
     ]
 
 

@@ -515,13 +515,8 @@ lshb_status run_batched(lshbloom *h, const uint64_t *offsets, const uint32_t *to
     uint64_t *d_off_stage = (uint64_t *)h->buf(B_OFFSTAGE).ptr;
 
     auto issue_copy = [&](size_t ci) -> lshb_status {
-        const int sb = (int)(ci & 1);
         const uint64_t t0 = off[chunks[ci].first], nt = off[chunks[ci].second] - t0;
-        BCK(cudaStreamWaitEvent(h->copy_stream, h->ev_stage_free[sb], 0));
-        if (nt) BCK(cudaMemcpyAsync(h->stage_tok[sb].ptr, tokens + t0, nt * 4, cudaMemcpyHostToDevice,
-                                    h->copy_stream));
-        BCK(cudaEventRecord(h->ev_stage_ready[sb], h->copy_stream));
-        return LSHB_OK;
+        return stage_copy(h, (int)(ci & 1), tokens + t0, nt);
     };
 
     for (size_t ci = 0; ci < chunks.size(); ++ci) {
@@ -564,6 +559,7 @@ lshb_status run_batched(lshbloom *h, const uint64_t *offsets, const uint32_t *to
         // a copy call that blocks the host then no longer idles the GPU.
         if (!tok_dev && ci + 1 < chunks.size() && (st = issue_copy(ci + 1)) != LSHB_OK) return st;
         BCK(cudaStreamSynchronize(s));
+        if (!tok_dev && (st = stage_copy_done(h, (int)(ci & 1))) != LSHB_OK) return st;
         float ms_k7 = 0.f;
         BCK(cudaEventElapsedTime(&ms_k7, b->ev0, b->ev1));
         if (keys_out)

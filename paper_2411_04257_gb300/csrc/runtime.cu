@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -197,6 +198,8 @@ lshbloom::~lshbloom() {
         if (host_stage_tok[i]) cudaFreeHost(host_stage_tok[i]);
         if (ev_stage_free[i]) cudaEventDestroy(ev_stage_free[i]);
         if (ev_stage_ready[i]) cudaEventDestroy(ev_stage_ready[i]);
+        for (int j = 0; j < 2; ++j)
+            if (ev_h2d[i][j]) cudaEventDestroy(ev_h2d[i][j]);
     }
     for (int i = 0; i < 3; ++i)
         if (ev_t[i]) cudaEventDestroy(ev_t[i]);
@@ -339,6 +342,8 @@ lshb_status lshb::init_handle(lshbloom *h, const lshb_config *cfg) {
     for (int i = 0; i < 2; ++i) {
         CK(cudaEventCreateWithFlags(&h->ev_stage_free[i], cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&h->ev_stage_ready[i], cudaEventDisableTiming));
+        CK(cudaEventCreate(&h->ev_h2d[i][0]));
+        CK(cudaEventCreate(&h->ev_h2d[i][1]));
     }
     for (int i = 0; i < 3; ++i) CK(cudaEventCreate(&h->ev_t[i]));
     for (int i = 0; i < 2; ++i) CK(cudaEventCreate(&h->ev_p[i]));
@@ -504,6 +509,36 @@ lshb_status lshb::ensure_stage(lshbloom *h, uint64_t Tc) {
         lshb_status st = h->stage_tok[i].reserve(std::max<uint64_t>(Tc, 1) * 4);
         if (st != LSHB_OK) return st;
     }
+    return LSHB_OK;
+}
+
+// Account the completed staging copy of buffer sb (its events bracket the
+// copy on the copy stream; it has finished once the chunk that read it has).
+lshb_status lshb::stage_copy_done(lshbloom *h, int sb) {
+    if (!h->h2d_pending[sb]) return LSHB_OK;
+    CK(cudaEventSynchronize(h->ev_h2d[sb][1]));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev_h2d[sb][0], h->ev_h2d[sb][1]));
+    h->t_h2d_ms += ms;
+    h->h2d_bytes += h->h2d_pending[sb];
+    h->h2d_pending[sb] = 0;
+    return LSHB_OK;
+}
+
+// Copy ntok host tokens into staging buffer sb on the copy stream once the
+// buffer is free; ev_stage_ready[sb] marks the end.
+lshb_status lshb::stage_copy(lshbloom *h, int sb, const uint32_t *src, uint64_t ntok) {
+    lshb_status st = stage_copy_done(h, sb);
+    if (st != LSHB_OK) return st;
+    CK(cudaStreamWaitEvent(h->copy_stream, h->ev_stage_free[sb], 0));
+    if (ntok) {
+        CK(cudaEventRecord(h->ev_h2d[sb][0], h->copy_stream));
+        CK(cudaMemcpyAsync(h->stage_tok[sb].ptr, src, ntok * 4, cudaMemcpyHostToDevice,
+                           h->copy_stream));
+        CK(cudaEventRecord(h->ev_h2d[sb][1], h->copy_stream));
+        h->h2d_pending[sb] = ntok * 4;
+    }
+    CK(cudaEventRecord(h->ev_stage_ready[sb], h->copy_stream));
     return LSHB_OK;
 }
 
@@ -724,13 +759,8 @@ static lshb_status run_batch(lshbloom *h, const uint64_t *offsets, const uint32_
     // Host tokens: chunk c+1 is copied on the copy stream into the other
     // staging buffer while chunk c computes.
     auto issue_copy = [&](size_t ci) -> lshb_status {
-        const int sb = (int)(ci & 1);
         const uint64_t t0 = off[chunks[ci].first], nt = off[chunks[ci].second] - t0;
-        CK(cudaStreamWaitEvent(h->copy_stream, h->ev_stage_free[sb], 0));
-        if (nt) CK(cudaMemcpyAsync(h->stage_tok[sb].ptr, tokens + t0, nt * 4, cudaMemcpyHostToDevice,
-                                   h->copy_stream));
-        CK(cudaEventRecord(h->ev_stage_ready[sb], h->copy_stream));
-        return LSHB_OK;
+        return stage_copy(h, (int)(ci & 1), tokens + t0, nt);
     };
     if (!tok_dev && !chunks.empty() && (st = issue_copy(0)) != LSHB_OK) return st;
     // The next chunk's copy is issued once this chunk's first kernels are
@@ -770,6 +800,7 @@ static lshb_status run_batch(lshbloom *h, const uint64_t *offsets, const uint32_
             if ((st = run_bloom(h, Dn, fl, s)) != LSHB_OK) return st;
             CK(cudaEventRecord(h->ev_t[2], s));
             CK(cudaEventSynchronize(h->ev_t[2]));
+            if (!tok_dev && (st = stage_copy_done(h, (int)(ci & 1))) != LSHB_OK) return st;
             float ms_sig = 0.f, ms_bloom = 0.f;
             CK(cudaEventElapsedTime(&ms_sig, h->ev_t[0], h->ev_t[1]));
             CK(cudaEventElapsedTime(&ms_bloom, h->ev_t[1], h->ev_t[2]));
@@ -800,13 +831,31 @@ static lshb_status run_batch(lshbloom *h, const uint64_t *offsets, const uint32_
         if (!tok_dev) CK(cudaEventRecord(h->ev_stage_free[ci & 1], s));
     }
     if (!require_device) CK(cudaStreamSynchronize(s));
+    if (!tok_dev)
+        for (int sb = 0; sb < 2; ++sb)
+            if ((st = stage_copy_done(h, sb)) != LSHB_OK) return st;
     return LSHB_OK;
+}
+
+// Dedup calls add their host wall-clock time to the handle's call_ms.
+static lshb_status run_batch_timed(lshbloom *h, const uint64_t *offsets, const uint32_t *tokens,
+                                   uint64_t D, void *out, Job job, cudaStream_t user_stream,
+                                   bool require_device, uint64_t *keys_out = nullptr) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const lshb_status st =
+        run_batch(h, offsets, tokens, D, out, job, user_stream, require_device, keys_out);
+    if (h && job == Job::Dedup) {
+        std::lock_guard<std::mutex> lock(h->mu);
+        h->t_call_ms +=
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return st;
 }
 
 extern "C" lshb_status lshbloom_dedup(lshbloom_t *h, const uint64_t *offsets,
                                       const uint32_t *tokens, uint64_t D, uint8_t *flags_out) {
     if (!h) return fail(LSHB_ERR_ARG, "NULL handle");
-    return run_batch(h, offsets, tokens, D, flags_out, Job::Dedup, nullptr, false);
+    return run_batch_timed(h, offsets, tokens, D, flags_out, Job::Dedup, nullptr, false);
 }
 
 extern "C" lshb_status lshbloom_dedup_keys(lshbloom_t *h, const uint64_t *offsets,
@@ -814,14 +863,14 @@ extern "C" lshb_status lshbloom_dedup_keys(lshbloom_t *h, const uint64_t *offset
                                            uint64_t *keys_out) {
     if (!h) return fail(LSHB_ERR_ARG, "NULL handle");
     if (D > 0 && !keys_out) return fail(LSHB_ERR_ARG, "NULL keys_out");
-    return run_batch(h, offsets, tokens, D, flags_out, Job::Dedup, nullptr, false, keys_out);
+    return run_batch_timed(h, offsets, tokens, D, flags_out, Job::Dedup, nullptr, false, keys_out);
 }
 
 extern "C" lshb_status lshbloom_dedup_async(lshbloom_t *h, const uint64_t *offsets,
                                             const uint32_t *tokens, uint64_t D, uint8_t *flags_out,
                                             void *stream) {
     if (!h) return fail(LSHB_ERR_ARG, "NULL handle");
-    return run_batch(h, offsets, tokens, D, flags_out, Job::Dedup, (cudaStream_t)stream, true);
+    return run_batch_timed(h, offsets, tokens, D, flags_out, Job::Dedup, (cudaStream_t)stream, true);
 }
 
 extern "C" lshb_status lshbloom_signatures(lshbloom_t *h, const uint64_t *offsets,
@@ -901,6 +950,9 @@ extern "C" lshb_status lshbloom_stats(lshbloom_t *h, lshb_stats *out) {
     out->sig_chunks = h->sig_chunks;
     out->probe_ms = h->t_probe_ms;
     out->probe_sectors = h->probe_sectors;
+    out->h2d_ms = h->t_h2d_ms;
+    out->h2d_bytes = h->h2d_bytes;
+    out->call_ms = h->t_call_ms;
     unsigned long long *cnt = (unsigned long long *)(h->counters + C_POPCOUNT);
     const bool exact = h->layout == LSHB_EXACT_KEYS;
     for (uint32_t j = 0; j < h->bands; ++j) {

@@ -72,6 +72,10 @@ struct lshbloom {
     cudaStream_t stream = nullptr, copy_stream = nullptr;
     cudaEvent_t ev_stage_free[2] = {nullptr, nullptr};
     cudaEvent_t ev_stage_ready[2] = {nullptr, nullptr};
+    cudaEvent_t ev_h2d[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // bracket each staging copy
+    uint64_t h2d_pending[2] = {0, 0};                                    // bytes of the copy in flight
+    double t_h2d_ms = 0.0, t_call_ms = 0.0;
+    uint64_t h2d_bytes = 0;
     lshb::DevBuf stage_tok[2];
     uint32_t *host_stage_tok[2] = {nullptr, nullptr};
     uint32_t *counters = nullptr;       // device, 64 x uint32
@@ -96,6 +100,11 @@ struct lshbloom {
 };
 
 namespace lshb {
+
+// Staging copies of host tokens into stage_tok[sb] on the copy stream, and
+// the accounting of the one that completed.
+lshb_status stage_copy(lshbloom *h, int sb, const uint32_t *src, uint64_t ntok);
+lshb_status stage_copy_done(lshbloom *h, int sb);
 
 lshb_status fail(lshb_status st, const char *fmt, ...);
 lshb_status cuda_fail(cudaError_t e, const char *what);
