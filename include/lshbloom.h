@@ -38,8 +38,12 @@
  *
  * Memory: pointers marked "host or device" may point to host memory (pageable
  * or pinned) or to device memory of the handle's GPU; the library finds out
- * which with cudaPointerGetAttributes and copies as needed.  The caller owns
- * all buffers it passes; the handle owns its filters and scratch.
+ * which with cudaPointerGetAttributes and copies as needed.  Page-locked
+ * (pinned) host tokens are not copied: the kernels read them in place through
+ * their device mapping (over NVLink-C2C on a Grace host), so they must stay
+ * unchanged until the call returns; pageable tokens are staged through
+ * device buffers.  The caller owns all buffers it passes; the handle owns its
+ * filters and scratch.
  *
  * CSR batches: document d of a batch of D documents is
  * tokens[offsets[d] .. offsets[d+1]-1]; offsets has D+1 non-decreasing

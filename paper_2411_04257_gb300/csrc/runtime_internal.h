@@ -110,6 +110,7 @@ lshb_status fail(lshb_status st, const char *fmt, ...);
 lshb_status cuda_fail(cudaError_t e, const char *what);
 lshb_status init_handle(lshbloom *h, const lshb_config *cfg);
 bool is_device_pointer(const void *p);
+const void *mapped_host_pointer(const void *p);
 lshb_status host_offsets(lshbloom *h, const uint64_t *offsets, uint64_t D, bool dev,
                          std::vector<uint64_t> &out);
 void plan_chunks(const lshbloom *h, const std::vector<uint64_t> &off, bool bound_tokens,

@@ -198,8 +198,33 @@ def test_dedup_many_calls_and_small_chunks(lshb, oracle, corpus):
 
 
 def test_dedup_host_inputs(lshb, oracle, corpus):
+    """Pageable host arrays: tokens staged through device buffers."""
     off, tok = _small_corpus(corpus, n=900)
     _check_dedup(lshb, oracle, off, tok, device_inputs=False, max_batch_docs=200)
+
+
+@pytest.mark.parametrize("exec_mode", ["batched", "plain"])
+def test_pinned_host_inputs_read_in_place(lshb, oracle, corpus, exec_mode):
+    """Page-locked host tensors: the kernels read the tokens through their
+    device mapping.  Flags over several calls and chunks, the final filters,
+    signatures and band keys all equal the oracle's."""
+    off, tok = _small_corpus(corpus, n=1200)
+    h_off = torch.from_numpy(off.view(np.int64)).pin_memory()
+    h_tok = torch.from_numpy(tok.view(np.int32)).pin_memory()
+    ix = lshb.LSHBloom(121, 11, 11, n_expected=1200, exec_mode=exec_mode, max_batch_docs=300)
+    ref = oracle.OracleIndex(121, 11, 11, n_expected=1200)
+    got = np.concatenate([np.asarray(ix.dedup(h_off[:601], h_tok)),
+                          np.asarray(ix.dedup(h_off[600:], h_tok))])
+    want = ref.dedup(off, tok)
+    assert np.array_equal(got, want) and want.sum() > 20
+    for j in range(11):
+        assert np.array_equal(ix.filter_bytes(j), ref.filter_bytes(j)), f"filter {j}"
+    sig = np.asarray(ix.signatures(h_off[:401], h_tok)).view(np.uint32)
+    osig = oracle.batch_signatures(off[:401], tok, 5, *oracle.coefficients(1, 121))
+    assert np.array_equal(sig, osig)
+    keys = np.asarray(ix.band_keys(h_off, h_tok)).view(np.uint64)
+    osig = oracle.batch_signatures(off, tok, 5, *oracle.coefficients(1, 121))
+    assert np.array_equal(keys, osig[:, :121].astype(np.uint64).reshape(-1, 11, 11).sum(axis=2))
 
 
 def test_identical_documents(lshb, oracle):
