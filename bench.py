@@ -463,6 +463,10 @@ def run_ours(args):
                "h2d_gbs_in_steps": ((s1["h2d_bytes"] - s0["h2d_bytes"])
                                     / max(1e-9, (s1["h2d_ms"] - s0["h2d_ms"]) / 1e3) / 1e9),
                "call_ms_per_step": (s1["call_ms"] - s0["call_ms"]) / args.steps,
+               # tokens the kernels read in place from the pinned buffers over
+               # the host link (no staging copy), per step
+               "host_read_bytes_per_step": (s1["host_read_bytes"] - s0["host_read_bytes"])
+                                           / args.steps,
                "clocks": ck.summary()}
         del h_tok
 

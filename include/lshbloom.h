@@ -38,11 +38,14 @@
  *
  * Memory: pointers marked "host or device" may point to host memory (pageable
  * or pinned) or to device memory of the handle's GPU; the library finds out
- * which with cudaPointerGetAttributes and copies as needed.  Page-locked
- * (pinned) host tokens are not copied: the kernels read them in place through
- * their device mapping (over NVLink-C2C on a Grace host), so they must stay
- * unchanged until the call returns; pageable tokens are staged through
- * device buffers.  The caller owns all buffers it passes; the handle owns its
+ * which with cudaPointerGetAttributes and copies as needed.  Host tokens are
+ * not copied where the GPU can read them: page-locked (pinned) buffers through
+ * their device mapping, and, on devices that report pageable-memory access
+ * through the host's page tables (a GB300 on a Grace host, over NVLink-C2C),
+ * pageable buffers too; the kernels then read them in place, so they must
+ * stay unchanged until the call returns.  Other host tokens, and all of them
+ * when lshb_config.stage_host_inputs is set, are staged through device
+ * buffers.  The caller owns all buffers it passes; the handle owns its
  * filters and scratch.
  *
  * CSR batches: document d of a batch of D documents is
@@ -126,7 +129,10 @@ typedef struct {
                                  the first chunk of a call ramped up from 2^28) */
     uint32_t item_shingles;   /* batched mode: shingles per work item, 0 = autotuned */
     uint32_t bloom_layout;    /* lshb_bloom_layout (default STANDARD) */
-    uint32_t reserved[6];
+    uint32_t stage_host_inputs; /* nonzero: always copy host tokens to the device through
+                                   staging buffers instead of letting the kernels read them
+                                   in place (see "Memory" above) */
+    uint32_t reserved[5];
 } lshb_config;
 
 typedef struct {
@@ -149,6 +155,7 @@ typedef struct {
     double h2d_ms;            /* copy-stream time of the token copies of host inputs (CUDA events) */
     uint64_t h2d_bytes;       /* bytes those copies moved */
     double call_ms;           /* host wall-clock time spent inside dedup calls */
+    uint64_t host_read_bytes; /* host token bytes the kernels read in place (no copy) */
 } lshb_stats;
 
 /* Fill *cfg with defaults: P=121, b=11, r=11, n=5, n_expected=10000,
@@ -298,7 +305,10 @@ LSHB_API lshb_status lshbloom_server_create(lshbloom_t *const *indexes, uint32_t
 
 /* Queue D documents (host offsets[D+1], host tokens) for index `index`; the
  * flags land in host flags_out[D].  The three buffers must stay valid until
- * the request completes.  *ticket identifies the request.  ERR_BUSY when the
+ * the request completes.  Offsets and tokens the GPU can read in place (see
+ * "Memory" above; none when an index of the server sets stage_host_inputs)
+ * are read by the kernels directly and take no budget; others are copied
+ * into the budget.  *ticket identifies the request.  ERR_BUSY when the
  * request alone needs more than the memory budget; ERR_CSR for decreasing
  * offsets. */
 LSHB_API lshb_status lshbloom_server_submit(lshbloom_server_t *s, uint32_t index,

@@ -66,7 +66,8 @@ class LSHBloom:
                  fp_rate: float = 1e-5, ngram: int = 5, seed: int = 1, insert_all: bool = False,
                  fp_is_effective: bool = False, exec_mode: str = "batched", device: int = -1,
                  max_batch_docs: int = 0, max_batch_tokens: int = 0, item_shingles: int = 0,
-                 perm_a=None, perm_b=None, bloom_layout: str = "standard", _handle=None):
+                 perm_a=None, perm_b=None, bloom_layout: str = "standard",
+                 stage_host_inputs: bool = False, _handle=None):
         self._h = None
         if _handle is not None:
             self._h = _handle
@@ -83,6 +84,7 @@ class LSHBloom:
         cfg.max_batch_docs, cfg.max_batch_tokens = max_batch_docs, max_batch_tokens
         cfg.item_shingles = item_shingles
         cfg.bloom_layout = _LAYOUTS[bloom_layout]
+        cfg.stage_host_inputs = 1 if stage_host_inputs else 0
         keep = []
         if perm_a is not None:
             pa = np.ascontiguousarray(perm_a, np.uint64)

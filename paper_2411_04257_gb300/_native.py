@@ -23,7 +23,8 @@ class Config(C.Structure):
         ("perm_a", C.POINTER(C.c_uint64)), ("perm_b", C.POINTER(C.c_uint64)),
         ("exec_mode", C.c_uint32), ("device", C.c_int32), ("max_batch_docs", C.c_uint64),
         ("max_batch_tokens", C.c_uint64), ("item_shingles", C.c_uint32),
-        ("bloom_layout", C.c_uint32), ("reserved", C.c_uint32 * 6),
+        ("bloom_layout", C.c_uint32), ("stage_host_inputs", C.c_uint32),
+        ("reserved", C.c_uint32 * 5),
     ]
 
 
@@ -38,6 +39,7 @@ class Stats(C.Structure):
         ("sig_ms", C.c_double), ("bloom_ms", C.c_double), ("sig_chunks", C.c_uint64),
         ("probe_ms", C.c_double), ("probe_sectors", C.c_uint64),
         ("h2d_ms", C.c_double), ("h2d_bytes", C.c_uint64), ("call_ms", C.c_double),
+        ("host_read_bytes", C.c_uint64),
     ]
 
 

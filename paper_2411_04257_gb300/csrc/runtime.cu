@@ -337,6 +337,7 @@ lshb_status lshb::init_handle(lshbloom *h, const lshb_config *cfg) {
     if (dev < 0) CK(cudaGetDevice(&dev));
     h->device = dev;
     CK(cudaSetDevice(dev));
+    h->pageable_access = device_reads_pageable(dev);
     CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
     CK(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
     for (int i = 0; i < 2; ++i) {
@@ -421,6 +422,22 @@ const void *lshb::mapped_host_pointer(const void *p) {
         return nullptr;
     }
     return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+const void *lshb::host_read_pointer(bool pageable_access, const void *p) {
+    if (const void *m = mapped_host_pointer(p)) return m;
+    return pageable_access ? p : nullptr;
+}
+
+bool lshb::device_reads_pageable(int device) {
+    int pma = 0, host_tables = 0;
+    if (cudaDeviceGetAttribute(&pma, cudaDevAttrPageableMemoryAccess, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&host_tables, cudaDevAttrPageableMemoryAccessUsesHostPageTables,
+                               device) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return pma && host_tables;
 }
 
 bool lshb::is_device_pointer(const void *p) {
@@ -738,21 +755,22 @@ static lshb_status run_batch(lshbloom *h, const uint64_t *offsets, const uint32_
     const bool keys_dev = keys_out && is_device_pointer(keys_out);
     if (require_device && (!off_dev || !tok_dev || !out_dev))
         return fail(LSHB_ERR_ARG, "lshbloom_dedup_async takes device pointers only");
-    // Page-locked host tokens are read in place by the kernels: measured on a
-    // GB300, the copy engine staging a batch ran at 40-100 GB/s while the
+    // Host tokens the GPU can read are read in place by the kernels: measured
+    // on a GB300, the copy engine staging a batch ran at 40-100 GB/s while the
     // signature kernel was running (211 GB/s alone), whereas the kernel's own
-    // reads over the host link cost it 1% of its time.  Pageable tokens are
-    // staged through device buffers.
-    if (!tok_dev) {
-        if (const void *m = mapped_host_pointer(tokens)) {
+    // reads over the host link cost it 1% of its time.  Others are staged.
+    bool tok_in_place = false;
+    if (!tok_dev && !h->cfg.stage_host_inputs) {
+        if (const void *m = host_read_pointer(h->pageable_access, tokens)) {
             tokens = (const uint32_t *)m;
-            tok_dev = true;
+            tok_dev = tok_in_place = true;
         }
     }
     cudaStream_t s = user_stream ? user_stream : h->stream;
     std::vector<uint64_t> off;
     lshb_status st = host_offsets(h, offsets, D, off_dev, off);
     if (st != LSHB_OK) return st;
+    if (tok_in_place && job == Job::Dedup) h->host_read_bytes += (off[D] - off[0]) * 4;
     if (job == Job::Dedup && h->cfg.exec_mode == LSHB_EXEC_BATCHED && h->passes.size() == 1) {
         return run_batched(h, offsets, tokens, D, (uint8_t *)out, off, off_dev, tok_dev, out_dev, s,
                            keys_out, keys_dev);
@@ -976,6 +994,7 @@ extern "C" lshb_status lshbloom_stats(lshbloom_t *h, lshb_stats *out) {
     out->h2d_ms = h->t_h2d_ms;
     out->h2d_bytes = h->h2d_bytes;
     out->call_ms = h->t_call_ms;
+    out->host_read_bytes = h->host_read_bytes;
     unsigned long long *cnt = (unsigned long long *)(h->counters + C_POPCOUNT);
     const bool exact = h->layout == LSHB_EXACT_KEYS;
     for (uint32_t j = 0; j < h->bands; ++j) {

@@ -75,7 +75,8 @@ struct lshbloom {
     cudaEvent_t ev_h2d[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // bracket each staging copy
     uint64_t h2d_pending[2] = {0, 0};                                    // bytes of the copy in flight
     double t_h2d_ms = 0.0, t_call_ms = 0.0;
-    uint64_t h2d_bytes = 0;
+    uint64_t h2d_bytes = 0, host_read_bytes = 0;
+    bool pageable_access = false;  // the device reads pageable host memory via host page tables
     lshb::DevBuf stage_tok[2];
     uint32_t *host_stage_tok[2] = {nullptr, nullptr};
     uint32_t *counters = nullptr;       // device, 64 x uint32
@@ -111,6 +112,11 @@ lshb_status cuda_fail(cudaError_t e, const char *what);
 lshb_status init_handle(lshbloom *h, const lshb_config *cfg);
 bool is_device_pointer(const void *p);
 const void *mapped_host_pointer(const void *p);
+// Address the kernels can read host buffer p through, or nullptr when it must
+// be staged: its device mapping when pinned, p itself when the device reads
+// pageable memory in place.
+const void *host_read_pointer(bool pageable_access, const void *p);
+bool device_reads_pageable(int device);
 lshb_status host_offsets(lshbloom *h, const uint64_t *offsets, uint64_t D, bool dev,
                          std::vector<uint64_t> &out);
 void plan_chunks(const lshbloom *h, const std::vector<uint64_t> &off, bool bound_tokens,

@@ -37,6 +37,8 @@ struct Request {
     uint64_t D = 0, T = 0, tok0 = 0;
     const uint64_t *h_off = nullptr;
     const uint32_t *h_tok = nullptr;
+    const uint64_t *in_off = nullptr;  // offsets / tokens the kernels read in place (or nullptr:
+    const uint32_t *in_tok = nullptr;  // copied into the budget)
     uint8_t *h_flags = nullptr;
     uint64_t bytes = 0, pool_off = 0;
     uint64_t *d_off = nullptr;
@@ -99,6 +101,8 @@ struct lshbloom_server {
     std::vector<lshbloom *> idx;
     int device = 0;
     uint32_t bands = 0;
+    bool pageable_access = false;  // the device reads pageable host memory in place
+    bool stage_inputs = false;     // an index asked for staged host inputs
     Pool pool;
     void *pool_mem = nullptr;
     std::vector<cudaStream_t> streams;
@@ -118,33 +122,41 @@ struct lshbloom_server {
     lshb_status bloom(Request *r);
 };
 
-static uint64_t request_bytes(uint64_t D, uint64_t T, uint32_t bands) {
-    return align256((D + 1) * 8) + align256(T * 4) + align256(D * bands * 8) + align256(D);
+// Budget of a request: its keys and flags, and the offsets and tokens that
+// are copied rather than read in place.
+static uint64_t request_bytes(uint64_t D, uint64_t T, uint32_t bands, bool copy_off, bool copy_tok) {
+    return (copy_off ? align256((D + 1) * 8) : 0) + (copy_tok ? align256(T * 4) : 0) +
+           align256(D * bands * 8) + align256(D);
 }
 
 lshb_status lshbloom_server::launch(Request *r) {
     cudaStream_t s = streams[r->slot];
     uint8_t *p = pool.base + r->pool_off;
-    r->d_off = (uint64_t *)p;
-    p += align256((r->D + 1) * 8);
-    r->d_tok = (uint32_t *)p;
-    p += align256(r->T * 4);
+    cudaError_t e;
+    if (!r->in_off) {
+        r->d_off = (uint64_t *)p;
+        p += align256((r->D + 1) * 8);
+        if ((e = cudaMemcpyAsync(r->d_off, r->h_off, (r->D + 1) * 8, cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess)
+            return cuda_fail(e, "request offsets");
+    }
+    if (!r->in_tok) {
+        r->d_tok = (uint32_t *)p;
+        p += align256(r->T * 4);
+        if (r->T && (e = cudaMemcpyAsync(r->d_tok, r->h_tok + r->tok0, r->T * 4,
+                                         cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return cuda_fail(e, "request tokens");
+    }
     r->d_keys = (uint64_t *)p;
     p += align256(r->D * bands * 8);
     r->d_flags = p;
-    cudaError_t e;
-    if ((e = cudaMemcpyAsync(r->d_off, r->h_off, (r->D + 1) * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess)
-        return cuda_fail(e, "request offsets");
-    if (r->T && (e = cudaMemcpyAsync(r->d_tok, r->h_tok + r->tok0, r->T * 4, cudaMemcpyHostToDevice, s)) !=
-                    cudaSuccess)
-        return cuda_fail(e, "request tokens");
     lshbloom *h = idx[r->index];
     const SigPass &ps = h->passes[0];
     SigArgs a;
     memset(&a, 0, sizeof a);
-    a.offsets = r->d_off;
-    a.tokens = r->d_tok;
-    a.tok_base = r->tok0;
+    a.offsets = r->in_off ? r->in_off : r->d_off;
+    a.tokens = r->in_tok ? r->in_tok : r->d_tok;
+    a.tok_base = r->in_tok ? 0 : r->tok0;
     a.D = r->D;
     a.ngram = h->ngram;
     a.P = h->P;
@@ -263,7 +275,11 @@ extern "C" lshb_status lshbloom_server_create(lshbloom_t *const *indexes, uint32
     s->idx.assign(indexes, indexes + n);
     s->device = indexes[0]->device;
     s->bands = 0;
-    for (auto *h : s->idx) s->bands = std::max(s->bands, h->bands);
+    for (auto *h : s->idx) {
+        s->bands = std::max(s->bands, h->bands);
+        s->stage_inputs = s->stage_inputs || h->cfg.stage_host_inputs;
+    }
+    s->pageable_access = device_reads_pageable(s->device);
     cudaSetDevice(s->device);
     cudaError_t e = cudaMalloc(&s->pool_mem, mem_budget_bytes);
     if (e != cudaSuccess) {
@@ -301,12 +317,16 @@ extern "C" lshb_status lshbloom_server_submit(lshbloom_server_t *s, uint32_t ind
     r->h_off = offsets;
     r->h_tok = tokens;
     r->h_flags = flags_out;
-    r->bytes = request_bytes(D, r->T, s->bands);
+    if (D && !s->stage_inputs) {
+        r->in_off = (const uint64_t *)host_read_pointer(s->pageable_access, offsets);
+        r->in_tok = (const uint32_t *)host_read_pointer(s->pageable_access, tokens);
+    }
+    r->bytes = request_bytes(D, r->T, s->bands, !r->in_off, !r->in_tok);
     if (r->bytes > s->pool.size) {
+        const uint64_t need = r->bytes;
         delete r;
         return fail(LSHB_ERR_BUSY, "request needs %llu bytes, the server budget is %llu",
-                    (unsigned long long)request_bytes(D, offsets[D] - offsets[0], s->bands),
-                    (unsigned long long)s->pool.size);
+                    (unsigned long long)need, (unsigned long long)s->pool.size);
     }
     r->t_submit = Clock::now();
     {

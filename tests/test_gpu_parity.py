@@ -197,10 +197,18 @@ def test_dedup_many_calls_and_small_chunks(lshb, oracle, corpus):
                  max_batch_docs=97, max_batch_tokens=5000)
 
 
-def test_dedup_host_inputs(lshb, oracle, corpus):
-    """Pageable host arrays: tokens staged through device buffers."""
+@pytest.mark.parametrize("stage", [True, False])
+def test_dedup_host_inputs(lshb, oracle, corpus, stage):
+    """Pageable host arrays: staged through device buffers (forced), or read in
+    place where the device reads pageable host memory (else staged)."""
     off, tok = _small_corpus(corpus, n=900)
-    _check_dedup(lshb, oracle, off, tok, device_inputs=False, max_batch_docs=200)
+    for mode in ("batched", "plain"):
+        want, st = _check_dedup(lshb, oracle, off, tok, device_inputs=False, max_batch_docs=200,
+                                exec_mode=mode, stage_host_inputs=stage)
+        if stage:
+            assert st["host_read_bytes"] == 0 and st["h2d_bytes"] == int(tok.nbytes)
+        else:
+            assert st["host_read_bytes"] + st["h2d_bytes"] == int(tok.nbytes)
 
 
 @pytest.mark.parametrize("exec_mode", ["batched", "plain"])
@@ -217,6 +225,8 @@ def test_pinned_host_inputs_read_in_place(lshb, oracle, corpus, exec_mode):
                           np.asarray(ix.dedup(h_off[600:], h_tok))])
     want = ref.dedup(off, tok)
     assert np.array_equal(got, want) and want.sum() > 20
+    st = ix.stats()
+    assert st["host_read_bytes"] == int(tok.nbytes) and st["h2d_bytes"] == 0
     for j in range(11):
         assert np.array_equal(ix.filter_bytes(j), ref.filter_bytes(j)), f"filter {j}"
     sig = np.asarray(ix.signatures(h_off[:401], h_tok)).view(np.uint32)

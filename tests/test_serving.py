@@ -79,22 +79,41 @@ def test_served_matches_oracle(lshb, oracle):
 
 
 def test_tight_budget_serialises_but_agrees(lshb):
+    """Requests copied into the budget (staged host inputs), at most one or
+    two of the largest in flight: same flags as plain sequential calls."""
     reqs = _requests(n_req=30, seed=5)
     want, _ = _sequential(lshb, reqs, exec_mode="plain")
     biggest = max(int(o[-1] - o[0]) * 4 + len(o) * 8 + (len(o) - 1) * 97 + 1024
                   for _, o, _ in reqs)
-    got, _, _ = _served(lshb, reqs, budget=biggest + 4096, inflight=3)
+    got, _, _ = _served(lshb, reqs, budget=biggest + 4096, inflight=3, stage_host_inputs=True)
     for g, w in zip(got, want):
         assert np.array_equal(g, w)
 
 
+def test_served_staged_equals_in_place(lshb):
+    """The same requests with their tokens copied into the budget and read in
+    place (where the device can) give the same flags and filters."""
+    reqs = _requests(n_req=40, seed=12)
+    a, _, ia = _served(lshb, reqs, stage_host_inputs=True)
+    b, _, ib = _served(lshb, reqs)
+    for g, w in zip(a, b):
+        assert np.array_equal(g, w)
+    for x, y in zip(ia, ib):
+        for j in range(11):
+            assert np.array_equal(x.filter_bytes(j), y.filter_bytes(j))
+
+
 def test_oversize_request_and_timeouts(lshb):
-    ix = lshb.LSHBloom(121, 11, 11)
+    ix = lshb.LSHBloom(121, 11, 11, stage_host_inputs=True)
     srv = lshb.LSHBloomServer([ix], mem_budget_bytes=1 << 16, max_inflight=2)
     off = np.array([0, 100_000], np.uint64)
     tok = np.arange(100_000, dtype=np.uint32)
-    with pytest.raises(lshb.LSHBloomError) as e:
+    with pytest.raises(lshb.LSHBloomError) as e:     # 400 KB of tokens to copy
         srv.submit(0, off, tok)
+    assert e.value.status == -7
+    many = np.arange(0, 2001, dtype=np.uint64)       # 2000 one-token documents:
+    with pytest.raises(lshb.LSHBloomError) as e:     # 176 KB of band keys alone
+        srv.submit(0, many, np.arange(2000, dtype=np.uint32))
     assert e.value.status == -7
     bad = np.array([0, 5, 3], np.uint64)
     with pytest.raises(lshb.LSHBloomError) as e:
