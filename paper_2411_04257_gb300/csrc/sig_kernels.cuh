@@ -107,6 +107,26 @@ __device__ __forceinline__ void fold4(uint32_t (&mn)[PPL], const LaneCoef<PPL> &
     }
 }
 
+// Hash of the NG-token shingle starting at lane `lane` of a 32-token step,
+// from that step's tokens (ta, one per lane) and the next step's (tb): the
+// window is assembled with shuffles.
+template <int NG>
+__device__ __forceinline__ uint32_t window_hash_regs(uint32_t ta, uint32_t tb, int lane) {
+    uint32_t w[NG];
+    w[0] = bswap32(ta);
+#pragma unroll
+    for (int k = 1; k < NG; ++k) {
+        const uint32_t v = lane >= k ? ta : tb;
+        w[k] = bswap32(__shfl_sync(LSHB_FULL_MASK, v, (lane + k) & 31));
+    }
+    return bswap32(sha1_h0_one_block<NG>(w));
+}
+
+// Token i of a document of L tokens, 0 past its end.
+__device__ __forceinline__ uint32_t token_or_zero(const uint32_t *tk, uint64_t i, uint64_t L) {
+    return i < L ? __ldg(tk + i) : 0u;
+}
+
 // Hash of shingle s0+lane of a document of L >= n tokens.  For NG > 0 the
 // window is assembled with shuffles from two coalesced loads; lanes past the
 // last shingle return an unspecified value.
@@ -114,21 +134,8 @@ template <int NG>
 __device__ __forceinline__ uint32_t window_hash(const uint32_t *tk, uint64_t L, uint64_t S,
                                                 uint64_t s0, int lane, uint32_t n) {
     if constexpr (NG > 0) {
-        const uint64_t ia = s0 + lane;
-        const uint32_t ta = ia < L ? __ldg(tk + ia) : 0u;
-        uint32_t tb = 0u;
-        if constexpr (NG > 1) {
-            const uint64_t ib = s0 + 32 + lane;
-            if (lane < NG - 1 && ib < L) tb = __ldg(tk + ib);
-        }
-        uint32_t w[NG];
-        w[0] = bswap32(ta);
-#pragma unroll
-        for (int k = 1; k < NG; ++k) {
-            const uint32_t v = lane >= k ? ta : tb;
-            w[k] = bswap32(__shfl_sync(LSHB_FULL_MASK, v, (lane + k) & 31));
-        }
-        return bswap32(sha1_h0_one_block<NG>(w));
+        return window_hash_regs<NG>(token_or_zero(tk, s0 + lane, L),
+                                    token_or_zero(tk, s0 + 32 + lane, L), lane);
     } else {
         uint64_t s = s0 + lane;
         if (s >= S) s = S - 1;
@@ -161,11 +168,20 @@ __device__ __forceinline__ void fold_pass(uint32_t (&mn)[PPL], const LaneCoef<PP
         }
         return;
     }
+    // For NG > 0 each step loads the next step's 32 tokens, which also hold
+    // the NG-1 tokens the current windows run into: one coalesced load per
+    // step, issued a whole step before its tokens are hashed.
+    uint32_t ta = 0u;
+    if constexpr (NG > 0) ta = hashes ? 0u : token_or_zero(tk, s_begin + lane, L);
     for (uint64_t s0 = s_begin; s0 < s_end; s0 += 32) {
         const uint32_t cnt = (uint32_t)min((uint64_t)32, s_end - s0);
         uint32_t h;
         if (hashes) {
             h = (s0 + lane < s_end) ? __ldg(hashes + s0 + lane) : 0u;
+        } else if constexpr (NG > 0) {
+            const uint32_t tn = token_or_zero(tk, s0 + 32 + lane, L);
+            h = window_hash_regs<NG>(ta, tn, lane);
+            ta = tn;
         } else {
             h = window_hash<NG>(tk, L, S, s0, lane, n);
         }
