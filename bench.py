@@ -31,13 +31,24 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    # name: (spec factory, n_docs, n_expected, fp_rate)
-    "pes2o_1m": ("pes2o_shaped", 1_000_000, 39_000_000, 1e-5),
+    # name: (spec factory, n_docs, n_expected, fp_rate, tokens, shingles); the
+    # token and shingle counts are those the generator gives rank 0 (checked)
+    "pes2o_1m": ("pes2o_shaped", 1_000_000, 39_000_000, 1e-5, 4_917_430_137, 4_913_430_137),
     # the first 100k documents of the same corpus, same filters (still > L2): profiling case
-    "pes2o_100k": ("pes2o_shaped", 100_000, 39_000_000, 1e-5),
-    "plain_10k": ("plain_10k", 10_000, 10_000, 1e-5),
+    "pes2o_100k": ("pes2o_shaped", 100_000, 39_000_000, 1e-5, 489_419_695, 489_019_695),
+    "plain_10k": ("plain_10k", 10_000, 10_000, 1e-5, 6_425_246, 6_385_246),
 }
 P, BANDS, ROWS, NGRAM = 121, 11, 11, 5
+METRIC = "docs/s (LSHBloom dedup: shingle SHA-1, MinHash P=121, 11x11 bands, Bloom query+insert)"
+
+
+def _config(name, world):
+    """The workload as both arms report it."""
+    _, D, nexp, fp, T, S = WORKLOADS[name]
+    return {"workload": f"{name}: {D} docs, {T} tokens, {S} shingles", "P": P, "bands": BANDS,
+            "rows": ROWS, "ngram": NGRAM, "n_expected": nexp, "fp_rate": fp,
+            "l2": "inputs larger than L2 (tokens %.1f GB)" % (T * 4 / 1e9),
+            "parallelism": f"replicas{world}"}
 SM_COUNT = 152
 IMAD_PER_SM_CLK = 64        # 32-bit integer multiply(-add) results per SM per clock
 SM_MAX_MHZ = 2070.0
@@ -148,7 +159,7 @@ def _rank_env():
 
 def _spec(name, rank):
     from synth import corpus
-    fac, n, nexp, fp = WORKLOADS[name]
+    fac, n, nexp, fp = WORKLOADS[name][:4]
     spec = getattr(corpus, fac)() if fac == "plain_10k" else getattr(corpus, fac)(n_docs=n)
     import dataclasses
     return dataclasses.replace(spec, seed=spec.seed + rank), nexp, fp
@@ -238,13 +249,14 @@ def run_reference(args):
             times.append(dt)
     total = sum(times)
     v = n * len(times) / total
-    line = {"impl": "reference", "metric": "docs/s (LSHBloom dedup)", "value": v, "unit": "docs/s",
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "docs/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": args.workload, "sample_docs": n},
+            "config": _config(args.workload, world),
             "cpu_baseline": {"value": v, "unit": "docs/s", "cores": 1, "kind": "oracle",
-                             "sample": f"first {n} docs of the workload per step"},
+                             "sample": f"first {n} docs of the workload per step "
+                                       f"({int(off[-1] - off[0])} tokens)"},
             "e2e": {"value": v, "unit": "docs/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -365,6 +377,9 @@ def run_ours(args):
     S = torch.where(L >= NGRAM, L - NGRAM + 1, (L > 0).to(L.dtype))
     shingles = int(S.sum().item())
     permhashes = shingles * P
+    if rank == 0 and (D, T, shingles) != (WORKLOADS[args.workload][1], *WORKLOADS[args.workload][4:]):
+        raise RuntimeError(f"generated corpus ({D} docs, {T} tokens, {shingles} shingles) differs "
+                           f"from the workload table")
 
     stream = torch.cuda.Stream(dev)
 
@@ -483,15 +498,12 @@ def run_ours(args):
     cpu = None if args.skip_cpu else _cpu_baseline(spec, nexp, fp)
     b = results["batched"]
     line = {
-        "metric": "docs/s (LSHBloom dedup: shingle SHA-1, MinHash P=121, 11x11 bands, Bloom query+insert)",
+        "metric": METRIC,
         "value": b["docs_per_s"], "unit": "docs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * b["seconds"] / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {D} docs, {T} tokens, {shingles} shingles",
-                   "P": P, "bands": BANDS, "rows": ROWS, "ngram": NGRAM, "n_expected": nexp,
-                   "fp_rate": fp, "l2": "inputs larger than L2 (tokens %.1f GB)" % (T * 4 / 1e9),
-                   "parallelism": f"replicas{world}"},
+        "config": _config(args.workload, world),
         "shingle_hashes_per_s": b["shingle_hashes_per_s"],
         "plain": ({"value": results["plain"]["docs_per_s"], "unit": "docs/s",
                    "shingle_hashes_per_s": results["plain"]["shingle_hashes_per_s"]}
@@ -541,7 +553,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="pes2o_1m", choices=sorted(WORKLOADS))
-    ap.add_argument("--ref-docs", type=int, default=150)
+    ap.add_argument("--ref-docs", type=int, default=1000)
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
