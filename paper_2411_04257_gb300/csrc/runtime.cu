@@ -195,7 +195,6 @@ lshbloom::~lshbloom() {
     for (auto &b : bufs) b.release();
     if (filters) cudaFree(filters);
     for (int i = 0; i < 2; ++i) {
-        if (host_stage_tok[i]) cudaFreeHost(host_stage_tok[i]);
         if (ev_stage_free[i]) cudaEventDestroy(ev_stage_free[i]);
         if (ev_stage_ready[i]) cudaEventDestroy(ev_stage_ready[i]);
         for (int j = 0; j < 2; ++j)
@@ -299,7 +298,6 @@ lshb_status lshb::init_handle(lshbloom *h, const lshb_config *cfg) {
     h->rows = cfg->rows;
     h->ngram = cfg->ngram;
     h->insert_all = cfg->insert_mode == LSHB_INSERT_ALL;
-    h->blocked = cfg->bloom_layout == LSHB_BLOOM_BLOCKED;
     h->layout = cfg->bloom_layout;
     h->p = cfg->fp_is_effective ? 1.0 - std::pow(1.0 - cfg->fp_rate, 1.0 / (double)cfg->bands)
                                 : cfg->fp_rate;

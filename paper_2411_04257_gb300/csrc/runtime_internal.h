@@ -62,7 +62,6 @@ struct lshbloom {
     int device = -1;
     uint32_t P = 0, bands = 0, rows = 0, ngram = 0, k = 0;
     bool insert_all = false;
-    bool blocked = false;  // 256-bit blocked filter layout
     uint32_t layout = 0;   // 0 standard, 1 blocked, 2 exact key sets
     double p = 0.0;
     uint64_t m = 0, words_per_filter = 0;
@@ -78,7 +77,6 @@ struct lshbloom {
     uint64_t h2d_bytes = 0, host_read_bytes = 0;
     bool pageable_access = false;  // the device reads pageable host memory via host page tables
     lshb::DevBuf stage_tok[2];
-    uint32_t *host_stage_tok[2] = {nullptr, nullptr};
     uint32_t *counters = nullptr;       // device, 64 x uint32
     uint32_t *host_counters = nullptr;  // pinned mirror
     lshb::DevBuf bufs[lshb::B_NBUF];
