@@ -317,6 +317,60 @@ def test_dedup_other_ngrams(lshb, oracle, corpus, ngram):
     _check_dedup(lshb, oracle, off, tok, ngram=ngram)
 
 
+@pytest.mark.parametrize("P", [300, 1024])
+def test_signatures_several_passes(lshb, oracle, corpus, P):
+    """More than 256 permutations: the signature runs in passes of up to 256
+    (two and four passes here), each folding every shingle again."""
+    off, tok = _small_corpus(corpus, n=250)
+    ix = lshb.LSHBloom(P, 16, 8, seed=3)
+    a, b = ix.coefficients()
+    got = ix.signatures(*_dev(off, tok)).cpu().numpy().view(np.uint32)
+    want = oracle.batch_signatures(off, tok, 5, a, b)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("exec_mode", ["batched", "plain"])
+def test_dedup_many_bands_and_passes(lshb, oracle, corpus, exec_mode):
+    """The largest band count (64 bands of 4 rows) on P = 300 (two signature
+    passes): flags and all 64 filters against the oracle."""
+    off, tok = _small_corpus(corpus, n=900, dup_frac=0.4)
+    ix = lshb.LSHBloom(300, 64, 4, n_expected=900, fp_rate=1e-4, exec_mode=exec_mode,
+                       max_batch_docs=400)
+    ref = oracle.OracleIndex(300, 64, 4, n_expected=900, fp_rate=1e-4)
+    got = np.concatenate([ix.dedup(*_dev(off[:451], tok)).cpu().numpy(),
+                          ix.dedup(*_dev(off[450:], tok)).cpu().numpy()])
+    want = ref.dedup(off, tok)
+    assert np.array_equal(got, want) and want.sum() > 50
+    for j in range(64):
+        assert np.array_equal(ix.filter_bytes(j), ref.filter_bytes(j)), f"filter {j}"
+
+
+@pytest.mark.parametrize("ngram", [13, 14, 64])
+def test_long_ngrams_around_the_document_length(lshb, oracle, ngram):
+    """n = 13 (the largest single-block SHA-1 message), 14 (two blocks) and 64
+    (five blocks), on documents of 0 .. 3n tokens, so that shorter-than-n,
+    exactly-n and longer documents all occur."""
+    rnd = np.random.default_rng(ngram)
+    lens = list(range(0, 3 * ngram + 2)) + list(rnd.integers(0, 400, size=60))
+    docs = [rnd.integers(0, 2**32, size=int(L), dtype=np.uint64).astype(np.uint32) for L in lens]
+    docs += [docs[-1].copy(), docs[ngram].copy()]           # exact copies
+    off, tok = _csr(docs)
+    ix = lshb.LSHBloom(121, 11, 11, ngram=ngram, n_expected=len(docs))
+    a, b = ix.coefficients()
+    got = ix.signatures(*_dev(off, tok)).cpu().numpy().view(np.uint32)
+    assert np.array_equal(got, oracle.batch_signatures(off, tok, ngram, a, b))
+    flags = ix.dedup(*_dev(off, tok)).cpu().numpy()
+    want = oracle.OracleIndex(121, 11, 11, ngram=ngram, n_expected=len(docs)).dedup(off, tok)
+    assert np.array_equal(flags, want) and want[-2:].tolist() == [1, 1]
+
+
+def test_largest_probe_count(lshb, oracle, corpus):
+    """p = 1e-18 per filter sizes k = 60 probes per key (the limit is 64)."""
+    off, tok = _small_corpus(corpus, n=700)
+    want, st = _check_dedup(lshb, oracle, off, tok, n_expected=700, fp_rate=1e-18)
+    assert st["k"] == oracle.sizing(700, 1e-18)[1] and 56 <= st["k"] <= 64
+
+
 def test_sizing_matches_oracle(lshb, oracle):
     for n, p, eff in [(10_000, 1e-5, False), (39_000_000, 1e-5, False), (1234, 0.01, False),
                       (10_000, 1e-10, True), (5_000, 1e-3, True)]:
