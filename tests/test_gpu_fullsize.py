@@ -90,6 +90,21 @@ def test_pes2o_shaped_1m(lshb, oracle):
     off, tok = gen.generate(0, spec.n_docs)
     ixp = lshb.LSHBloom(121, 11, 11, n_expected=39_000_000, fp_rate=1e-5, exec_mode="plain")
     assert np.array_equal(ixp.dedup(off, tok).cpu().numpy(), flags)
+    ixp.close()
+    # and so does the batch from page-locked host memory (the bench's e2e leg:
+    # 19.7 GB of tokens read in place by the kernels), filters included
+    h_off = torch.empty(off.shape, dtype=off.dtype, pin_memory=True)
+    h_tok = torch.empty(tok.shape, dtype=tok.dtype, pin_memory=True)
+    h_off.copy_(off)
+    h_tok.copy_(tok)
+    del off, tok
+    torch.cuda.empty_cache()
+    ixh = lshb.LSHBloom(121, 11, 11, n_expected=39_000_000, fp_rate=1e-5)
+    assert np.array_equal(np.asarray(ixh.dedup(h_off, h_tok)), flags)
+    st = ixh.stats()
+    assert st["host_read_bytes"] == h_tok.numel() * 4 and st["h2d_bytes"] == 0
+    for j in (0, 10):
+        assert np.array_equal(ixh.filter_bytes(j), ix.filter_bytes(j))
 
 
 def test_pareto_batched_8m(lshb, oracle):
