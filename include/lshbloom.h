@@ -103,6 +103,16 @@ typedef enum {
     LSHB_EXACT_KEYS = 2
 } lshb_bloom_layout;
 
+/* Band key of b bands of r signature rows x_0 .. x_{r-1} (band j).  SUM is
+ * the paper's reduction, (sum_t x_t) mod 2^64 (Sec. 4.1, the Carter-Wegman
+ * form with the signature values as the per-row hashes).  WEIGHTED is a
+ * variant beyond the paper: (sum_t c_{j,t} x_t) mod 2^64 with fixed odd
+ * weights c_{j,t} = SplitMix64-finaliser(0x9e3779b97f4a7c15 * ((j << 10) + t
+ * + 1)) | 1.  Minima of many shingles cluster near 0, so plain sums of
+ * unrelated documents collide far more often than 2^-32; the weights restore
+ * a bound of about 2^-32 for distinct bands. */
+typedef enum { LSHB_BAND_SUM = 0, LSHB_BAND_WEIGHTED = 1 } lshb_band_key;
+
 typedef enum {
     LSHB_EXEC_PLAIN = 0,   /* one kernel per stage */
     LSHB_EXEC_BATCHED = 1  /* persistent fused kernel over a work queue, graph-launched */
@@ -132,7 +142,8 @@ typedef struct {
     uint32_t stage_host_inputs; /* nonzero: always copy host tokens to the device through
                                    staging buffers instead of letting the kernels read them
                                    in place (see "Memory" above) */
-    uint32_t reserved[5];
+    uint32_t band_key;        /* lshb_band_key (default SUM, the paper's) */
+    uint32_t reserved[4];
 } lshb_config;
 
 typedef struct {

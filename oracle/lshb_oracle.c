@@ -189,6 +189,27 @@ OR_API void or_band_keys(const uint32_t *sig, uint32_t bands, uint32_t rows, uin
     }
 }
 
+/* Weighted band key, a variant beyond the paper: sum_t c_{j,t} x_t mod 2^64
+ * with c_{j,t} the SplitMix64 output number (j << 10) + t + 1 of seed 0 (the
+ * finaliser of (j << 10 + t + 1) times the golden gamma), made odd.  Mode 0 is
+ * the paper's plain sum (or_band_keys). */
+OR_API void or_band_keys_mode(const uint32_t *sig, uint32_t bands, uint32_t rows, uint32_t mode,
+                              uint64_t *keys) {
+    if (mode == 0) {
+        or_band_keys(sig, bands, rows, keys);
+        return;
+    }
+    for (uint32_t j = 0; j < bands; ++j) {
+        uint64_t s = 0;
+        for (uint32_t t = 0; t < rows; ++t) {
+            const uint64_t idx = ((uint64_t)j << 10) + t + 1;
+            const uint64_t c = or_mix64(idx * 0x9e3779b97f4a7c15ull) | 1ull;
+            s += c * sig[j * rows + t];
+        }
+        keys[j] = s;
+    }
+}
+
 /* Probe positions of a band key in its band's Bloom filter, Sec. 2.4 (k hash
  * functions into a bit array of m bits).  The paper names no hash family.
  * Reading: Kirsch-Mitzenmacher double hashing (ESA 2006) on SplitMix64
@@ -456,6 +477,7 @@ typedef struct {
     uint32_t layout;     /* 0: standard filter (Sec. 2.4), 1: 256-bit blocked variant,
                             2: exact band-key sets */
     void *sets;          /* layout 2: one or_keyset per band */
+    uint32_t band_key;   /* 0: the paper's sum, 1: weighted sum (or_band_keys_mode) */
     uint64_t m;          /* bits per filter */
     uint64_t words;      /* 64-bit words per filter */
     uint64_t *a, *b;     /* permutation coefficients */
@@ -545,6 +567,13 @@ OR_API int or_index_set_layout(or_index *ix, uint32_t layout) {
     return 0;
 }
 
+/* Band-key mode of an index (before its first document). */
+OR_API int or_index_set_band_key(or_index *ix, uint32_t mode) {
+    if (mode > 1) return -1;
+    ix->band_key = mode;
+    return 0;
+}
+
 /* Keys of band j of an exact index (unordered); returns how many. */
 OR_API uint64_t or_index_exact_keys(const or_index *ix, uint32_t j, uint64_t *out, uint64_t cap) {
     if (ix->layout != 2) return 0;
@@ -600,7 +629,7 @@ OR_API void or_index_dedup(or_index *ix, const uint64_t *offsets, const uint32_t
     for (uint64_t i = 0; i < D; ++i) {
         uint64_t L = offsets[i + 1] - offsets[i];
         or_signature(tokens + offsets[i], L, ix->ngram, ix->P, ix->a, ix->b, sig);
-        or_band_keys(sig, ix->bands, ix->rows, keys);
+        or_band_keys_mode(sig, ix->bands, ix->rows, ix->band_key, keys);
         int dup = 0;
         if (ix->layout == 2) {
             or_keyset *sets = (or_keyset *)ix->sets;

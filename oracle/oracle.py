@@ -60,6 +60,9 @@ def lib():
                 "or_probe_positions_blocked": (None, [C.c_uint64, C.c_uint32, C.c_uint64,
                                                       C.c_uint32, u64p]),
                 "or_index_set_layout": (C.c_int, [C.c_void_p, C.c_uint32]),
+                "or_index_set_band_key": (C.c_int, [C.c_void_p, C.c_uint32]),
+                "or_band_keys_mode": (None, [C.POINTER(C.c_uint32), C.c_uint32, C.c_uint32,
+                                             C.c_uint32, u64p]),
                 "or_index_exact_keys": (C.c_uint64, [C.c_void_p, C.c_uint32, u64p, C.c_uint64]),
                 "or_p_from_effective": (C.c_double, [C.c_double, C.c_uint32]),
                 "or_effective_from_p": (C.c_double, [C.c_double, C.c_uint32]),
@@ -153,10 +156,15 @@ def signature(tokens, n: int, a: np.ndarray, b: np.ndarray) -> np.ndarray:
     return sig
 
 
-def band_keys(sig: np.ndarray, bands: int, rows: int) -> np.ndarray:
+def band_keys(sig: np.ndarray, bands: int, rows: int, mode: int = 0) -> np.ndarray:
+    """Band keys of one signature: the paper's sums (mode 0) or the weighted
+    sums (mode 1)."""
     s = _u32(sig)
     keys = np.zeros(bands, np.uint64)
-    lib().or_band_keys(_p(s, C.c_uint32), bands, rows, _p(keys, C.c_uint64))
+    if mode == 0:
+        lib().or_band_keys(_p(s, C.c_uint32), bands, rows, _p(keys, C.c_uint64))
+    else:
+        lib().or_band_keys_mode(_p(s, C.c_uint32), bands, rows, mode, _p(keys, C.c_uint64))
     return keys
 
 
@@ -265,7 +273,7 @@ class OracleIndex:
                  fp_rate: float = 1e-5, ngram: int = 5, seed: int = 1,
                  insert_all: bool = False, fp_is_effective: bool = False,
                  m: int | None = None, k: int | None = None, a=None, b=None,
-                 layout: int = 0):
+                 layout: int = 0, band_key: int = 0):
         p = p_from_effective(fp_rate, bands) if fp_is_effective else fp_rate
         mm, kk = sizing_blocked(n_expected, p) if layout == 1 else sizing(n_expected, p)
         self.m = int(m) if m is not None else mm
@@ -281,6 +289,8 @@ class OracleIndex:
             raise ValueError("oracle index: bad parameters")
         if layout and lib().or_index_set_layout(self._h, layout) != 0:
             raise ValueError("oracle index: bad layout")
+        if band_key and lib().or_index_set_band_key(self._h, band_key) != 0:
+            raise ValueError("oracle index: bad band-key mode")
 
     def close(self):
         if getattr(self, "_h", None):

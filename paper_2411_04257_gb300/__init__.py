@@ -67,7 +67,7 @@ class LSHBloom:
                  fp_is_effective: bool = False, exec_mode: str = "batched", device: int = -1,
                  max_batch_docs: int = 0, max_batch_tokens: int = 0, item_shingles: int = 0,
                  perm_a=None, perm_b=None, bloom_layout: str = "standard",
-                 stage_host_inputs: bool = False, _handle=None):
+                 stage_host_inputs: bool = False, band_key: str = "sum", _handle=None):
         self._h = None
         if _handle is not None:
             self._h = _handle
@@ -85,6 +85,7 @@ class LSHBloom:
         cfg.item_shingles = item_shingles
         cfg.bloom_layout = _LAYOUTS[bloom_layout]
         cfg.stage_host_inputs = 1 if stage_host_inputs else 0
+        cfg.band_key = {"sum": 0, "weighted": 1}[band_key]
         keep = []
         if perm_a is not None:
             pa = np.ascontiguousarray(perm_a, np.uint64)

@@ -24,7 +24,7 @@ class Config(C.Structure):
         ("exec_mode", C.c_uint32), ("device", C.c_int32), ("max_batch_docs", C.c_uint64),
         ("max_batch_tokens", C.c_uint64), ("item_shingles", C.c_uint32),
         ("bloom_layout", C.c_uint32), ("stage_host_inputs", C.c_uint32),
-        ("reserved", C.c_uint32 * 5),
+        ("band_key", C.c_uint32), ("reserved", C.c_uint32 * 4),
     ]
 
 

@@ -37,7 +37,7 @@ struct DynParams {
 
 struct BatchArgs {
     DynParams *dyn;
-    uint32_t item_shingles, ngram, P, npc, bands, rows, k, sketch_log2, layout;
+    uint32_t item_shingles, ngram, P, npc, bands, rows, k, sketch_log2, layout, band_key;
     uint64_t m_bits, words_per_filter;
     const uint32_t *filters;
     uint32_t *item_count;      // D
@@ -211,8 +211,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batched(const __grid_constant
         for (int t = 0; t < PPL; ++t) sigbuf[lane + 32 * t] = mn[t];
         __syncwarp();
         for (uint32_t j = lane; j < A.bands; j += 32) {
-            uint64_t key = 0;
-            for (uint32_t t = 0; t < A.rows; ++t) key += sigbuf[j * A.rows + t];
+            const uint64_t key = band_key_of(sigbuf + j * A.rows, A.rows, j, A.band_key);
             A.keys[d * A.bands + j] = key;
             A.miss[d * A.bands + j] =
                 probe_band(A.filters + (uint64_t)j * A.words_per_filter, A.words_per_filter, key, j, A.k,
@@ -327,6 +326,7 @@ static BatchArgs make_args(lshbloom *h, BatchedState *b) {
     a.rows = h->rows;
     a.k = h->k;
     a.layout = h->layout;
+    a.band_key = h->cfg.band_key;
     a.m_bits = h->m;
     a.words_per_filter = h->words_per_filter;
     a.filters = h->filters;

@@ -119,6 +119,21 @@ __device__ __forceinline__ uint32_t sha1_h0_tokens(const uint32_t *tok, uint32_t
 
 __device__ __forceinline__ uint32_t shingle_hash_from_h0(uint32_t h0) { return bswap32(h0); }
 
+// Band key j of a signature band row[0 .. rows): the paper's sum (mode 0) or
+// the weighted sum with odd weights mix64(G ((j << 10) + t + 1)) | 1 (mode 1,
+// beyond the paper), mod 2^64.
+__host__ __device__ __forceinline__ uint64_t band_key_of(const uint32_t *row, uint32_t rows,
+                                                         uint32_t j, uint32_t mode) {
+    uint64_t s = 0;
+    if (mode == 0) {
+        for (uint32_t t = 0; t < rows; ++t) s += row[t];
+    } else {
+        for (uint32_t t = 0; t < rows; ++t)
+            s += (mix64(kGolden * (((uint64_t)j << 10) + t + 1)) | 1ull) * row[t];
+    }
+    return s;
+}
+
 // Probe sequence of one band key (library convention).  Standard layout:
 // Kirsch-Mitzenmacher double hashing over the m bits.  Blocked layout (the
 // variant beyond the paper): one 256-bit block per key, each position an

@@ -30,6 +30,7 @@ struct SigArgs {
     uint32_t p0;              // first permutation of this pass
     uint32_t npc;             // permutations in this pass (<= the kernel's PC)
     uint32_t bands, rows;     // band-key epilogue (used when keys_out != nullptr)
+    uint32_t band_key;        // lshb_band_key
     uint32_t *sig_out;        // D x P, or nullptr
     uint64_t *keys_out;       // D x bands, or nullptr
     const uint32_t *hashes;   // minhash-from-hashes input, indexed like tokens
@@ -49,6 +50,6 @@ cudaError_t launch_sig_ng5(int ppl, const SigArgs &a, cudaStream_t s);
 cudaError_t launch_shingle_hash(int ngram_tmpl, const SigArgs &a, cudaStream_t s);
 cudaError_t launch_minhash_hashes(int ppl, const SigArgs &a, cudaStream_t s);
 cudaError_t launch_band_keys(const uint32_t *sig, uint32_t P, uint32_t bands, uint32_t rows,
-                             uint64_t D, uint64_t *keys, cudaStream_t s);
+                             uint32_t band_key, uint64_t D, uint64_t *keys, cudaStream_t s);
 
 }  // namespace lshb

@@ -94,6 +94,7 @@ extern "C" LSHB_API lshb_status lshbloom_band_keys_static(lshbloom_t *h, const u
 
     SigArgs a;
     memset(&a, 0, sizeof a);
+    a.band_key = h->cfg.band_key;
     a.offsets = offsets;
     a.tokens = tokens;
     a.tok_base = 0;
@@ -113,7 +114,7 @@ extern "C" LSHB_API lshb_status lshbloom_band_keys_static(lshbloom_t *h, const u
         else e = launch_sig_ng0(ps.ppl, a, s);
         if (e != cudaSuccess) return cuda_fail(e, "signature kernel");
     }
-    if ((e = launch_band_keys(sig, h->P, h->bands, h->rows, D, keys_out, s)) != cudaSuccess)
+    if ((e = launch_band_keys(sig, h->P, h->bands, h->rows, h->cfg.band_key, D, keys_out, s)) != cudaSuccess)
         return cuda_fail(e, "band-key kernel");
     return LSHB_OK;
 }

@@ -239,6 +239,7 @@ static lshb_status validate_config(const lshb_config *c) {
         return fail(LSHB_ERR_ARG, "bands*rows (%u) exceeds num_perm (%u)", c->bands * c->rows,
                     c->num_perm);
     if (c->ngram < 1 || c->ngram > 64) return fail(LSHB_ERR_ARG, "ngram must be 1..64");
+    if (c->band_key > LSHB_BAND_WEIGHTED) return fail(LSHB_ERR_ARG, "band_key must be 0 or 1");
     if (c->n_expected < 1) return fail(LSHB_ERR_ARG, "n_expected must be >= 1");
     if (!(c->fp_rate > 0.0 && c->fp_rate < 1.0)) return fail(LSHB_ERR_ARG, "fp_rate must be in (0,1)");
     if (c->insert_mode > 1) return fail(LSHB_ERR_ARG, "bad insert_mode");
@@ -577,6 +578,7 @@ lshb_status lshb::run_signatures(lshbloom *h, const ChunkIn &in, uint32_t *sig_o
     const int ngt = ngram_template(h->ngram);
     SigArgs a;
     memset(&a, 0, sizeof a);
+    a.band_key = h->cfg.band_key;
     a.offsets = in.offsets;
     a.tokens = in.tokens;
     a.tok_base = in.tok_base;
@@ -612,7 +614,7 @@ lshb_status lshb::run_signatures(lshbloom *h, const ChunkIn &in, uint32_t *sig_o
         }
     }
     if (want_keys && (!single || plain))
-        CK(launch_band_keys(sig, h->P, h->bands, h->rows, in.D, keys, s));
+        CK(launch_band_keys(sig, h->P, h->bands, h->rows, h->cfg.band_key, in.D, keys, s));
     return LSHB_OK;
 }
 
@@ -1017,7 +1019,7 @@ struct FileHeader {
     uint32_t version, P, bands, rows, ngram, k, insert_mode, bloom_layout;
     uint64_t n_expected, seed, m_bits, words_per_filter, docs_seen, dups_seen;
     double fp_rate_cfg, p;
-    int32_t fp_is_effective, reserved1;
+    int32_t fp_is_effective, band_key;
 };
 }  // namespace
 
@@ -1036,6 +1038,7 @@ extern "C" lshb_status lshbloom_save(lshbloom_t *h, const char *path) {
     hd.words_per_filter = h->words_per_filter; hd.docs_seen = h->docs_seen;
     hd.dups_seen = h->dups_seen; hd.fp_rate_cfg = h->cfg.fp_rate; hd.p = h->p;
     hd.fp_is_effective = h->cfg.fp_is_effective;
+    hd.band_key = (int32_t)h->cfg.band_key;
     FILE *f = fopen(path, "wb");
     if (!f) return fail(LSHB_ERR_IO, "cannot open %s for writing", path);
     bool ok = fwrite(&hd, sizeof hd, 1, f) == 1;
@@ -1078,6 +1081,7 @@ extern "C" lshb_status lshbloom_load(const char *path, int32_t device, lshbloom_
     c.n_expected = hd.n_expected; c.fp_rate = hd.fp_rate_cfg; c.fp_is_effective = hd.fp_is_effective;
     c.insert_mode = hd.insert_mode; c.seed = hd.seed; c.perm_a = a.data(); c.perm_b = b.data();
     c.bloom_layout = hd.bloom_layout;
+    c.band_key = (uint32_t)hd.band_key;
     c.device = device;
     lshbloom_t *h = nullptr;
     lshb_status st = lshbloom_create_ex(&c, &h);

@@ -154,6 +154,7 @@ lshb_status lshbloom_server::launch(Request *r) {
     const SigPass &ps = h->passes[0];
     SigArgs a;
     memset(&a, 0, sizeof a);
+    a.band_key = h->cfg.band_key;
     a.offsets = r->in_off ? r->in_off : r->d_off;
     a.tokens = r->in_tok ? r->in_tok : r->d_tok;
     a.tok_base = r->in_tok ? 0 : r->tok0;

@@ -245,11 +245,8 @@ __device__ __forceinline__ void sig_epilogue(const SigArgs &A, uint64_t d, uint3
 #pragma unroll
         for (int t = 0; t < PPL; ++t) sigbuf[lane + 32 * t] = mn[t];
         __syncwarp();
-        for (uint32_t j = lane; j < A.bands; j += 32) {
-            uint64_t s = 0;
-            for (uint32_t t = 0; t < A.rows; ++t) s += sigbuf[j * A.rows + t];
-            A.keys_out[d * A.bands + j] = s;
-        }
+        for (uint32_t j = lane; j < A.bands; j += 32)
+            A.keys_out[d * A.bands + j] = band_key_of(sigbuf + j * A.rows, A.rows, j, A.band_key);
         __syncwarp();
     }
 }

@@ -48,28 +48,27 @@ cudaError_t launch_minhash_hashes(int ppl, const SigArgs &a, cudaStream_t s) {
     return launch_sig_ng0(ppl, a, s);
 }
 
-// Band key j of document d: sum of signature rows j*r .. j*r+r-1 (mod 2^64).
+// Band key j of document d from signature rows j*r .. j*r+r-1 (mod 2^64).
 __global__ void k_band_keys(const uint32_t *__restrict__ sig, uint32_t P, uint32_t bands,
-                            uint32_t rows, uint64_t D, uint64_t *__restrict__ keys) {
+                            uint32_t rows, uint32_t band_key, uint64_t D,
+                            uint64_t *__restrict__ keys) {
     const uint64_t n = D * bands;
     for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
          idx += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t d = idx / bands;
         const uint32_t j = (uint32_t)(idx % bands);
-        const uint32_t *row = sig + d * P + (uint64_t)j * rows;
-        uint64_t s = 0;
-        for (uint32_t t = 0; t < rows; ++t) s += row[t];
-        keys[idx] = s;
+        keys[idx] = band_key_of(sig + d * P + (uint64_t)j * rows, rows, j, band_key);
     }
 }
 
 cudaError_t launch_band_keys(const uint32_t *sig, uint32_t P, uint32_t bands, uint32_t rows,
-                             uint64_t D, uint64_t *keys, cudaStream_t s) {
+                             uint32_t band_key, uint64_t D, uint64_t *keys, cudaStream_t s) {
     const uint64_t n = D * bands;
     uint64_t blocks = (n + 255) / 256;
     if (blocks == 0) blocks = 1;
     if (blocks > 65535ull * 16) blocks = 65535ull * 16;
-    k_band_keys<<<(unsigned)blocks, 256, 0, s>>>(sig, P, bands, rows, D, keys); count_launch();
+    k_band_keys<<<(unsigned)blocks, 256, 0, s>>>(sig, P, bands, rows, band_key, D, keys);
+    count_launch();
     return cudaGetLastError();
 }
 

@@ -136,10 +136,36 @@ def test_band_keys(lshb, oracle, corpus, exec_mode):
     assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("exec_mode", ["batched", "plain"])
+def test_weighted_band_keys(lshb, oracle, corpus, exec_mode, tmp_path):
+    """Weighted band keys (beyond the paper): keys of both signature kernels
+    and of the batched kernel, then flags and filters over a save/load
+    continuation, against the oracle's weighted mode."""
+    off, tok = _small_corpus(corpus, n=900, dup_frac=0.4)
+    ix = lshb.LSHBloom(121, 11, 11, n_expected=900, band_key="weighted", exec_mode=exec_mode,
+                       max_batch_docs=300)
+    sig = oracle.batch_signatures(off, tok, 5, *oracle.coefficients(1, 121))
+    want_keys = np.stack([oracle.band_keys(g, 11, 11, mode=1) for g in sig])
+    assert np.array_equal(ix.band_keys(*_dev(off, tok)).cpu().numpy().view(np.uint64), want_keys)
+    ref = oracle.OracleIndex(121, 11, 11, n_expected=900, band_key=1)
+    f1, k1 = ix.dedup_keys(*_dev(off[:451], tok))
+    assert np.array_equal(k1.cpu().numpy().view(np.uint64), want_keys[:450])
+    path = str(tmp_path / "weighted.lshb")
+    ix.save(path)
+    ix2 = lshb.LSHBloom.load(path)
+    got = np.concatenate([f1.cpu().numpy(), ix2.dedup(*_dev(off[450:], tok)).cpu().numpy()])
+    want = ref.dedup(off, tok)
+    assert np.array_equal(got, want) and want.sum() > 50
+    for j in range(11):
+        assert np.array_equal(ix2.filter_bytes(j), ref.filter_bytes(j)), f"filter {j}"
+
+
 def _check_dedup(lshb, oracle, off, tok, calls=None, device_inputs=True, **kw):
     kw.setdefault("n_expected", max(len(off) - 1, 1))
     okw = {k: v for k, v in kw.items() if k in ("n_expected", "fp_rate", "ngram", "seed",
                                                   "insert_all", "fp_is_effective")}
+    if "band_key" in kw:
+        okw["band_key"] = {"sum": 0, "weighted": 1}[kw["band_key"]]
     ix = lshb.LSHBloom(121, 11, 11, **kw)
     ref = oracle.OracleIndex(121, 11, 11, **okw)
     D = len(off) - 1

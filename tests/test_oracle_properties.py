@@ -349,3 +349,28 @@ def test_blocked_stream_semantics(oracle):
     assert ix.dedup(off, toks).tolist() == [0, 1, 0]
     for j in range(11):
         assert ix.popcount(j) <= 2 * 17
+
+
+# --- weighted band keys (a variant beyond the paper) ------------------------------
+
+def test_weighted_band_keys_separate_what_sums_merge(oracle):
+    """Band tuples of small values, as minima of long documents are: their
+    plain sums (the paper's keys) collapse onto a few thousand values, while
+    the weighted sums keep every distinct tuple distinct; mode 0 is the plain
+    row sum; the same tuple in two bands gets two keys."""
+    rnd = np.random.default_rng(91)
+    n, r = 20_000, 11
+    tuples = rnd.integers(0, 512, size=(n, r), dtype=np.uint32)
+    distinct = len({t.tobytes() for t in tuples})
+    sums = {int(oracle.band_keys(t, 1, r)[0]) for t in tuples}
+    weighted = {int(oracle.band_keys(t, 1, r, mode=1)[0]) for t in tuples}
+    assert len(sums) < 6_000 < distinct
+    assert len(weighted) == distinct
+    t = tuples[0]
+    assert int(oracle.band_keys(t, 1, r)[0]) == int(t.astype(np.uint64).sum())
+    two = oracle.band_keys(np.concatenate([t, t]), 2, r, mode=1)
+    assert two[0] != two[1]
+    # keys are linear in the tuple (a weighted sum): k(x + y) = k(x) + k(y) mod 2^64
+    x, y = tuples[1] // 2, tuples[2] // 2
+    kx, ky, kxy = (int(oracle.band_keys(v, 1, r, mode=1)[0]) for v in (x, y, x + y))
+    assert kxy == (kx + ky) % 2**64
