@@ -394,12 +394,15 @@ def run_ours(args):
     item_shingles = None
     modes = ["batched", "plain"] if not args.skip_plain else ["batched"]
     if args.variants:
-        modes += ["batched/blocked", "plain/blocked", "batched/exact", "plain/exact"]
+        modes += ["batched/blocked", "plain/blocked", "batched/exact", "plain/exact",
+                  "batched/weighted"]
     index_bytes = {}
     for mode in modes:
-        layout = mode.split("/")[1] if "/" in mode else "standard"
+        variant = mode.split("/")[1] if "/" in mode else "standard"
+        layout = variant if variant in ("blocked", "exact") else "standard"
         ix = LSHBloom(P, BANDS, ROWS, n_expected=nexp, fp_rate=fp, ngram=NGRAM,
-                      exec_mode=mode.split("/")[0], device=local, bloom_layout=layout)
+                      exec_mode=mode.split("/")[0], device=local, bloom_layout=layout,
+                      band_key="weighted" if variant == "weighted" else "sum")
         st0 = ix.stats()
         index_bytes[layout] = st0["filter_bytes"] * st0["bands"]
 
@@ -534,7 +537,13 @@ def run_ours(args):
                                "standard": {"index_bytes": index_bytes["standard"],
                                             "dups_per_step": b["dups_per_step"],
                                             "bloom_stage_ms_per_step":
-                                                stage["batched"]["bloom_ms"] / args.steps}}
+                                                stage["batched"]["bloom_ms"] / args.steps},
+                               # standard filters, weighted band keys (beyond the paper)
+                               "weighted_band_keys": {
+                                   "batched_docs_per_s": results["batched/weighted"]["docs_per_s"],
+                                   "dups_per_step": results["batched/weighted"]["dups_per_step"],
+                                   "bloom_stage_ms_per_step":
+                                       stage["batched/weighted"]["bloom_ms"] / args.steps}}
                            if args.variants else None),
         "serve": serve,
         "item_shingles": item_shingles,
