@@ -64,7 +64,7 @@ IMAD_PER_PERMHASH = 4       # two 32x32->64 products (lo and hi halves) per (a*h
 _CSRC = "paper_2411_04257_gb300/csrc/"
 _TRAFFIC = {
     "k_batched": {"bytes_per_doc": 55030.0,
-                  "sources": ["batched.cu", "sig_kernels.cuh", "lshb_device.cuh",
+                  "sources": ["batched_kernels.cuh", "sig_kernels.cuh", "lshb_device.cuh",
                               "bloom_kernels.cuh", "lshb_internal.h"],
                   "sha256": "0dec289dbf43d9309d906624609638758b3e95ed47f4db04b38780b11d5ee952",
                   "profile": "profiles/dram_traffic_pes2o100k.md"},

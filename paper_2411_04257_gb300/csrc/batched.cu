@@ -19,208 +19,10 @@
 #include <algorithm>
 #include <cstring>
 
+#include "batched_kernels.cuh"
 #include "runtime_internal.h"
-#include "sig_kernels.cuh"
 
 namespace lshb {
-
-constexpr int kBatchThreads = 64;
-constexpr uint32_t kItemCandidates[] = {64, 128, 256, 512, 1024};
-
-struct DynParams {
-    const uint64_t *offsets;  // D+1
-    const uint32_t *tokens;   // document d at tokens[offsets[d] - tok_base]
-    uint64_t tok_base;
-    uint64_t D;
-    uint64_t n_items;         // written on the device by the scan
-};
-
-struct BatchArgs {
-    DynParams *dyn;
-    uint32_t item_shingles, ngram, P, npc, bands, rows, k, sketch_log2, layout, band_key;
-    uint64_t m_bits, words_per_filter;
-    const uint32_t *filters;
-    uint32_t *item_count;      // D
-    uint64_t *item_start;      // D+1
-    uint64_t *block_sums;      // scan partials
-    uint32_t *item_doc;        // n_items
-    uint64_t item_cap;         // capacity of item_doc
-    uint32_t *pending;         // D: items of the document not finished yet
-    uint32_t *sig_partial;     // D x P: merged minima of split documents
-    unsigned long long *queue;
-    uint64_t *keys, *miss, *cand;
-    uint8_t *prehit;
-    uint32_t *sketch1, *sketch2;
-    uint32_t *error;
-    PermSlice c;
-};
-
-__device__ __forceinline__ uint64_t items_of(uint64_t L, uint32_t n, uint32_t item) {
-    const uint64_t S = shingle_count(L, n);
-    return S == 0 ? 1 : (S + item - 1) / item;
-}
-
-// Per document: item count, pending counter, cleared Bloom-stage flags and,
-// for a document split over several items, a signature row of 2^32-1.
-__global__ void k_batch_prepare(const __grid_constant__ BatchArgs A) {
-    const DynParams dp = *A.dyn;
-    for (uint64_t d = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; d < dp.D;
-         d += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t L = dp.offsets[d + 1] - dp.offsets[d];
-        const uint64_t it = items_of(L, A.ngram, A.item_shingles);
-        A.item_count[d] = (uint32_t)it;
-        A.pending[d] = (uint32_t)it;
-        A.cand[d] = 0;
-        A.prehit[d] = 0;
-        if (it > 1) {
-            uint32_t *row = A.sig_partial + d * A.P;
-            for (uint32_t p = 0; p < A.P; ++p) row[p] = 0xffffffffu;
-        }
-    }
-}
-
-// Exclusive scan of item counts into item_start (D+1 entries), three phases.
-constexpr int kScanBlock = 1024;
-
-__device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t *tot) {
-    __shared__ uint64_t warp_sums[32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint64_t x = v;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const uint64_t y = __shfl_up_sync(LSHB_FULL_MASK, x, off);
-        if (lane >= off) x += y;
-    }
-    if (lane == 31) warp_sums[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        uint64_t s = warp_sums[lane];
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const uint64_t y = __shfl_up_sync(LSHB_FULL_MASK, s, off);
-            if (lane >= off) s += y;
-        }
-        warp_sums[lane] = s;  // inclusive over warps
-    }
-    __syncthreads();
-    const uint64_t before = (w > 0 ? warp_sums[w - 1] : 0) + x - v;
-    if (tot) *tot = warp_sums[31];
-    __syncthreads();
-    return before;
-}
-
-__global__ void __launch_bounds__(kScanBlock) k_scan_reduce(const __grid_constant__ BatchArgs A) {
-    const uint64_t D = A.dyn->D;
-    const uint64_t i = (uint64_t)blockIdx.x * kScanBlock + threadIdx.x;
-    uint64_t tot = 0;
-    block_exclusive_scan(i < D ? A.item_count[i] : 0, &tot);
-    if (threadIdx.x == 0) A.block_sums[blockIdx.x] = tot;
-}
-
-__global__ void __launch_bounds__(kScanBlock) k_scan_top(const __grid_constant__ BatchArgs A,
-                                                         uint32_t nb) {
-    __shared__ uint64_t carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (uint32_t base = 0; base < nb; base += kScanBlock) {
-        const uint32_t i = base + threadIdx.x;
-        uint64_t tot = 0;
-        const uint64_t ex = block_exclusive_scan(i < nb ? A.block_sums[i] : 0, &tot);
-        if (i < nb) A.block_sums[i] = carry + ex;
-        __syncthreads();
-        if (threadIdx.x == 0) carry += tot;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        A.dyn->n_items = carry;
-        if (carry > A.item_cap) atomicOr(A.error, kErrQueue);
-    }
-}
-
-__global__ void __launch_bounds__(kScanBlock) k_scan_down(const __grid_constant__ BatchArgs A) {
-    const uint64_t D = A.dyn->D;
-    const uint64_t i = (uint64_t)blockIdx.x * kScanBlock + threadIdx.x;
-    const uint64_t ex = block_exclusive_scan(i < D ? A.item_count[i] : 0, nullptr);
-    if (i < D) A.item_start[i] = A.block_sums[blockIdx.x] + ex;
-    if (i == 0) A.item_start[D] = A.dyn->n_items;
-}
-
-__global__ void k_expand(const __grid_constant__ BatchArgs A) {
-    const uint64_t D = A.dyn->D;
-    const uint64_t cap = A.item_cap;
-    for (uint64_t d = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; d < D;
-         d += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t s = A.item_start[d], n = A.item_count[d];
-        for (uint64_t t = 0; t < n && s + t < cap; ++t) A.item_doc[s + t] = (uint32_t)d;
-    }
-}
-
-// The persistent kernel.  Every warp pops items until the queue is drained;
-// nothing waits on another warp, so the kernel cannot stall.
-template <int NG, int PPL>
-__global__ void __launch_bounds__(kBatchThreads) k_batched(const __grid_constant__ BatchArgs A) {
-    __shared__ SigSmem<PPL> sm;
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const uint32_t n = NG > 0 ? (uint32_t)NG : A.ngram;
-    LaneCoef<PPL> cf;
-    cf.load(A.c, A.npc, lane);
-    uint32_t *hbuf = reinterpret_cast<uint32_t *>(sm.hbuf[wib]);
-    uint32_t *sigbuf = sm.sig[wib];
-    const DynParams dp = *A.dyn;
-    const uint64_t n_items = min(dp.n_items, A.item_cap);
-    for (;;) {
-        unsigned long long it = 0;
-        if (lane == 0) it = atomicAdd(A.queue, 1ull);
-        it = __shfl_sync(LSHB_FULL_MASK, it, 0);
-        if (it >= n_items) break;
-        const uint64_t d = A.item_doc[it];
-        const uint64_t ibeg = A.item_start[d];
-        const uint64_t icnt = A.item_start[d + 1] - ibeg;
-        if (d >= dp.D || it < ibeg || it - ibeg >= icnt) {
-            if (lane == 0) atomicOr(A.error, kErrQueue);
-            continue;
-        }
-        const uint64_t o0 = dp.offsets[d];
-        const uint64_t L = dp.offsets[d + 1] - o0;
-        const uint32_t *tk = dp.tokens + (o0 - dp.tok_base);
-        const uint64_t S = shingle_count(L, n);
-        const uint64_t s_begin = (it - ibeg) * A.item_shingles;
-        const uint64_t s_end = min(S, s_begin + A.item_shingles);
-        uint32_t mn[PPL];
-        fold_range<NG, PPL>(mn, cf, tk, L, n, s_begin, s_end, nullptr, hbuf, lane);
-        if (icnt > 1) {
-            uint32_t *row = A.sig_partial + d * A.P;
-#pragma unroll
-            for (int t = 0; t < PPL; ++t)
-                if (lane + 32 * t < (int)A.npc) atomicMin(row + lane + 32 * t, mn[t]);
-            __threadfence();
-            __syncwarp();
-            uint32_t last = 0;
-            if (lane == 0) last = atomicSub(A.pending + d, 1u) == 1u;
-            last = __shfl_sync(LSHB_FULL_MASK, last, 0);
-            if (!last) continue;
-            __threadfence();
-#pragma unroll
-            for (int t = 0; t < PPL; ++t)
-                if (lane + 32 * t < (int)A.npc) mn[t] = __ldcg(row + lane + 32 * t);
-        }
-        // band keys (Sec. 4.1) and the probes of this document (Sec. 4.2)
-        __syncwarp();
-#pragma unroll
-        for (int t = 0; t < PPL; ++t) sigbuf[lane + 32 * t] = mn[t];
-        __syncwarp();
-        for (uint32_t j = lane; j < A.bands; j += 32) {
-            const uint64_t key = band_key_of(sigbuf + j * A.rows, A.rows, j, A.band_key);
-            A.keys[d * A.bands + j] = key;
-            A.miss[d * A.bands + j] =
-                probe_band(A.filters + (uint64_t)j * A.words_per_filter, A.words_per_filter, key, j, A.k,
-                           A.m_bits, A.layout,
-                           A.sketch1, A.sketch2, A.sketch_log2);
-        }
-        __syncwarp();
-    }
-}
 
 // ---- host side ---------------------------------------------------------------------
 
@@ -486,6 +288,8 @@ lshb_status run_batched(lshbloom *h, const uint64_t *offsets, const uint32_t *to
                         uint8_t *flags, const std::vector<uint64_t> &off, bool off_dev,
                         bool tok_dev, bool out_dev, cudaStream_t s, uint64_t *keys_out,
                         bool keys_dev) {
+    if (off.size() != D + 1) return fail(LSHB_ERR_ARG, "offsets of %llu documents expected",
+                                         (unsigned long long)D);
     // chunks: documents and (for staged or very large inputs) tokens bounded
     const uint64_t dmax = h->max_docs_batched;
     std::vector<std::pair<uint64_t, uint64_t>> chunks;
