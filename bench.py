@@ -63,15 +63,15 @@ IMAD_PER_PERMHASH = 4       # two 32x32->64 products (lo and hi halves) per (a*h
 # sources hash to the captured state: a changed kernel reports null.
 _CSRC = "paper_2411_04257_gb300/csrc/"
 _TRAFFIC = {
-    "k_batched": {"bytes_per_doc": 55030.0,
+    "k_batched": {"bytes_per_doc": 55150.0,
                   "sources": ["batched_kernels.cuh", "sig_kernels.cuh", "lshb_device.cuh",
                               "bloom_kernels.cuh", "lshb_internal.h"],
-                  "sha256": "0dec289dbf43d9309d906624609638758b3e95ed47f4db04b38780b11d5ee952",
+                  "sha256": "43f6d52c6bcda82f074c30785e4fa79d53a6cf08868b08b71d38f807b760056e",
                   "profile": "profiles/dram_traffic_pes2o100k.md"},
-    "k_probe_mark": {"bytes_per_doc": 25379.0,
+    "k_probe_mark": {"bytes_per_doc": 24807.0,
                      "sources": ["bloom_kernels.cu", "bloom_kernels.cuh", "lshb_device.cuh",
                                  "lshb_internal.h"],
-                     "sha256": "8424cd037d953293fed1a434a16c5d7d46c6d23d2192a648f613dd5db69800a7",
+                     "sha256": "d967948eba240ac0171ffa157c944de8521a263bd42fccc0ba34f76044075788",
                      "profile": "profiles/dram_traffic_pes2o100k.md"},
 }
 
