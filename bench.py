@@ -120,6 +120,28 @@ def _probe_roofline(st, standard_layout=True):
                                  "(standard layout), b = 11 (blocked layout)"}
 
 
+def _clocks_rejected(c):
+    """A timed run that saw a hardware or thermal slowdown, or SM clocks well
+    below their maximum with no reason given (a leftover clock lock)."""
+    if not c or c.get("sm_mhz") is None:
+        return False
+    bad = {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
+    if bad & set(c.get("reasons", [])):
+        return True
+    return not c.get("reasons") and c["sm_mhz"] < 0.9 * c["sm_max_mhz"]
+
+
+def _any_rank(flag, device=None):
+    """The flag OR-reduced over ranks, so that all ranks take the same branch."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return bool(flag)
+    t = torch.tensor([1.0 if flag else 0.0], device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return bool(t.item() > 0)
+
+
 def _h2d_probe(h_src, d_dst, nbytes=4 << 30):
     """Best of three pinned host->device copies of up to 4 GB, in GB/s."""
     import torch
@@ -411,12 +433,20 @@ def run_ours(args):
             with torch.cuda.stream(stream):
                 ix.dedup_async(off, tok, stream=stream)
 
-        s0 = {}
-        with Clocks(local) as ck:
-            dt = _time_steps(step, args.steps, args.warmup, stream, barrier_sync,
-                             on_start=lambda: s0.update(ix.stats()))
-        clocks = ck.summary()
-        s1 = ix.stats()
+        rejected = None
+        for attempt in range(2):
+            s0 = {}
+            with Clocks(local) as ck:
+                dt = _time_steps(step, args.steps, args.warmup, stream, barrier_sync,
+                                 on_start=lambda: s0.update(ix.stats()))
+            clocks = ck.summary()
+            s1 = ix.stats()
+            if attempt == 0 and _any_rank(_clocks_rejected(clocks), dev):
+                rejected = clocks          # measured under a slowdown: once more
+                continue
+            break
+        if rejected is not None:
+            clocks["rejected_first_run"] = rejected
         if mode == "batched":
             item_shingles = s1["item_shingles"]
         launches[mode] = s1["kernel_launches"] - s0["kernel_launches"]
@@ -456,16 +486,25 @@ def run_ours(args):
             ixe.reset()
             ixe.dedup(h_off, h_tok, out=h_flags)
         h2d_gbs = _h2d_probe(h_tok, tok)
-        barrier_sync()
-        s0 = ixe.stats()
-        with Clocks(local) as ck:
-            t0 = time.perf_counter()
-            for _ in range(args.steps):
-                ixe.reset()
-                ixe.dedup(h_off, h_tok, out=h_flags)
+        rejected = None
+        for attempt in range(2):
             barrier_sync()
-            et = time.perf_counter() - t0
-        s1 = ixe.stats()
+            s0 = ixe.stats()
+            with Clocks(local) as ck:
+                t0 = time.perf_counter()
+                for _ in range(args.steps):
+                    ixe.reset()
+                    ixe.dedup(h_off, h_tok, out=h_flags)
+                barrier_sync()
+                et = time.perf_counter() - t0
+            s1 = ixe.stats()
+            e2e_clocks = ck.summary()
+            if attempt == 0 and _any_rank(_clocks_rejected(e2e_clocks), dev):
+                rejected = e2e_clocks
+                continue
+            break
+        if rejected is not None:
+            e2e_clocks["rejected_first_run"] = rejected
         et, docs = reduce_over_ranks(et, float(D * args.steps), dev)
         ixe.close()
         e2e = {"value": docs / et, "unit": "docs/s",
@@ -485,7 +524,7 @@ def run_ours(args):
                # the host link (no staging copy), per step
                "host_read_bytes_per_step": (s1["host_read_bytes"] - s0["host_read_bytes"])
                                            / args.steps,
-               "clocks": ck.summary()}
+               "clocks": e2e_clocks}
         del h_tok
 
     serve = None
