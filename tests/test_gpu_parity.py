@@ -437,3 +437,30 @@ def test_reset_and_errors(lshb, corpus):
     with pytest.raises(lshb.LSHBloomError):
         lshb.LSHBloom(121, 12, 11)
     assert ix.dedup(*_dev(off[:1], tok)).numel() == 0
+
+
+@pytest.mark.parametrize("layout,band_key", [("standard", "weighted"), ("blocked", "sum"),
+                                             ("blocked", "weighted"), ("exact", "sum"),
+                                             ("exact", "weighted")])
+@pytest.mark.parametrize("insert_all", [False, True])
+@pytest.mark.parametrize("exec_mode", ["batched", "plain"])
+def test_option_combinations(lshb, oracle, corpus, layout, band_key, insert_all, exec_mode):
+    """Every filter layout with both band-key modes, both insert rules and
+    both forms, over two calls: flags and the final index equal the oracle's."""
+    off, tok = _small_corpus(corpus, n=700, seed=31, dup_frac=0.4)
+    lay = {"standard": 0, "blocked": 1, "exact": 2}[layout]
+    ix = lshb.LSHBloom(121, 11, 11, n_expected=700, fp_rate=1e-4, bloom_layout=layout,
+                       band_key=band_key, insert_all=insert_all, exec_mode=exec_mode)
+    ref = oracle.OracleIndex(121, 11, 11, n_expected=700, fp_rate=1e-4, layout=lay,
+                             band_key=1 if band_key == "weighted" else 0, insert_all=insert_all)
+    got = np.concatenate([ix.dedup(*_dev(off[:351], tok)).cpu().numpy(),
+                          ix.dedup(*_dev(off[350:], tok)).cpu().numpy()])
+    want = ref.dedup(off, tok)
+    assert np.array_equal(got, want) and want.sum() > 30
+    for j in (0, 5, 10):
+        fb = ix.filter_bytes(j)
+        if layout == "exact":
+            t = fb.view(np.uint64)
+            assert np.array_equal(np.sort(t[t != np.uint64(2**64 - 1)]), ref.exact_keys(j))
+        else:
+            assert np.array_equal(fb, ref.filter_bytes(j))

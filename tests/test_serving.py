@@ -128,3 +128,15 @@ def test_oversize_request_and_timeouts(lshb):
     assert flags.tolist() == [0, 0] and lat > 0
     srv.close()
     ix.close()
+
+
+@pytest.mark.parametrize("layout,band_key", [("blocked", "weighted"), ("exact", "sum")])
+def test_served_other_layouts_equal_alone(lshb, layout, band_key):
+    """The server drives the Bloom stage of any layout and band-key mode: each
+    request's flags equal plain sequential calls on indexes of that kind."""
+    reqs = _requests(n_req=30, seed=17)
+    kw = dict(bloom_layout=layout, band_key=band_key)
+    want, _ = _sequential(lshb, reqs, **kw)
+    got, _, _ = _served(lshb, reqs, **kw)
+    for g, w in zip(got, want):
+        assert np.array_equal(g, w)
