@@ -200,8 +200,8 @@ __device__ __forceinline__ void fold_pass(uint32_t (&mn)[PPL], const LaneCoef<PP
 
 // The exact pass, kept out of line: inlined next to the fast pass it raised
 // the persistent kernel from 95 to 122 registers (8 instead of 10 blocks per
-// SM) and cost 17% of its throughput; called, it costs a stack frame on a
-// path taken about once per 2^29 / (shingles x permutations) ranges.
+// SM) and measured 14% slower; called, it costs a stack frame on a path that
+// a range takes with probability about (shingles x permutations) / 2^29.
 template <int NG, int PPL>
 __device__ __noinline__ void fold_exact(uint32_t (&mn)[PPL], const LaneCoef<PPL> &cf,
                                         const uint32_t *tk, uint64_t L, uint32_t n,

@@ -54,3 +54,14 @@ def test_clock_records_that_are_measured_again():
         assert bench._clocks_rejected({**ok, "reasons": [r]})
     assert bench._clocks_rejected({**ok, "sm_mhz": 1200.0})        # stuck low, no reason
     assert not bench._clocks_rejected({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]})
+
+
+def test_traffic_fingerprint_ignores_comments_only():
+    """The DRAM traffic bench.py reports was captured on a given kernel source;
+    its fingerprint ignores comments but not code."""
+    import bench
+    src = "// head\\n__global__ void k(int *p) {\\n    p[0] = 1;  /* one */\\n}\\n"
+    same = "/* new text */\\n__global__ void k(int *p) {   \\n    p[0] = 1;  // one\\n\\n}\\n"
+    other = "__global__ void k(int *p) {\\n    p[0] = 2;\\n}\\n"
+    fp = lambda text: bench._sources_sha256(["x.cu"], read=lambda rel: text)
+    assert fp(src) == fp(same) and fp(src) != fp(other)
