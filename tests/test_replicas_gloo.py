@@ -60,8 +60,8 @@ def test_traffic_fingerprint_ignores_comments_only():
     """The DRAM traffic bench.py reports was captured on a given kernel source;
     its fingerprint ignores comments but not code."""
     import bench
-    src = "// head\\n__global__ void k(int *p) {\\n    p[0] = 1;  /* one */\\n}\\n"
-    same = "/* new text */\\n__global__ void k(int *p) {   \\n    p[0] = 1;  // one\\n\\n}\\n"
-    other = "__global__ void k(int *p) {\\n    p[0] = 2;\\n}\\n"
+    src = "// head\n__global__ void k(int *p) {\n    p[0] = 1;  /* one */\n}\n"
+    same = "/* new text */\n__global__ void k(int *p) {   \n    p[0] = 1;  // one\n\n}\n"
+    other = "__global__ void k(int *p) {\n    p[0] = 2;\n}\n"
     fp = lambda text: bench._sources_sha256(["x.cu"], read=lambda rel: text)
     assert fp(src) == fp(same) and fp(src) != fp(other)
