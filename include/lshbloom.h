@@ -21,12 +21,14 @@
  *   - permutation i: ((a_i h + b_i) mod (2^61 - 1)) mod 2^32, exact on the
  *     93-bit product; (a_i, b_i) drawn from a SplitMix64 stream of `seed` in
  *     the order a_0, b_0, a_1, ...: a = 1 + x mod (2^61 - 2), b = x mod (2^61 - 1);
- *   - band key j: sum of rows j*r .. j*r+r-1, modulo 2^64;
+ *   - band key j: sum of rows j*r .. j*r+r-1, modulo 2^64 (a weighted sum
+ *     when lshb_config.band_key = LSHB_BAND_WEIGHTED, see lshb_band_key);
  *   - probes: x = mix64(key ^ j*0x9e3779b97f4a7c15), y = mix64(x ^
  *     0x6a09e667f3bcc909) | 1, q_u = high64((x + u*y) * m), u < k
  *     (Kirsch-Mitzenmacher double hashing; mix64 is the SplitMix64 finaliser);
  *   - filter size m = ceil(-n ln p / (ln 2)^2) rounded up to a multiple of 256
- *     bits (Sec. 4.5), k = max(1, round(m/n ln 2)); p_eff splits as
+ *     bits (Sec. 4.5), k = max(1, round(m/n ln 2)) (the blocked layout has
+ *     its own rule, see lshbloom_filter_sizing); p_eff splits as
  *     p = 1 - (1 - p_eff)^(1/b) (Sec. 4.3);
  *   - insert rule: by default only documents judged not duplicate are
  *     inserted (Sec. 4.4.2); LSHB_INSERT_ALL inserts every document.
