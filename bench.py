@@ -621,7 +621,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-serve", action="store_true")
     ap.add_argument("--variants", action="store_true",
-                    help="also measure the blocked filter layout and the exact band-key index")
+                    help="also measure the blocked filter layout, the exact band-key index "
+                         "and weighted band keys")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
