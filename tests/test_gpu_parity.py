@@ -126,6 +126,35 @@ def test_signatures_at_constructed_residues(lshb, oracle, corpus, P):
     assert np.array_equal(keys.cpu().numpy().view(np.uint64), keys_want)
 
 
+def test_single_shingle_minimum_of_all_ones(lshb, oracle):
+    """Documents of exactly n tokens have one shingle, so its permuted value is
+    the signature entry.  Coefficients put that value on 2^32 - 1 (residues
+    2^32 - 1 and 2^33 - 1) for half of the permutations: the entry must be
+    2^32 - 1, which an accumulation of value + 1 would wrap to 0."""
+    rnd = np.random.default_rng(4)
+    docs = [rnd.integers(0, 2**32, size=5, dtype=np.uint64).astype(np.uint32) for _ in range(64)]
+    docs += [rnd.integers(0, 2**32, size=3, dtype=np.uint64).astype(np.uint32) for _ in range(8)]
+    off, tok = _csr(docs)
+    hashes, counts = oracle.batch_shingle_hashes(off, tok, 5)
+    assert np.all(counts == 1)
+    P = 64
+    a = rnd.integers(1 << 40, MERSENNE - 1, size=P, dtype=np.uint64)
+    b = rnd.integers(0, MERSENNE, size=P, dtype=np.uint64)
+    for i in range(0, P, 2):                       # permutation i sends doc i's shingle to -1
+        h = int(hashes[i % len(docs)])
+        tau = (1 << 32) - 1 if i % 4 == 0 else (1 << 33) - 1
+        b[i] = (tau - int(a[i]) * h) % MERSENNE
+    want = oracle.batch_signatures(off, tok, 5, a, b)
+    assert (want == 0xFFFFFFFF).sum() >= P // 2
+    for mode in ("batched", "plain"):
+        ix = lshb.LSHBloom(P, 8, 4, perm_a=a, perm_b=b, exec_mode=mode)
+        got = ix.signatures(*_dev(off, tok)).cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, want), mode
+        sig = want.astype(np.uint64)[:, :32].reshape(-1, 8, 4).sum(axis=2)
+        _, keys = ix.dedup_keys(*_dev(off, tok))
+        assert np.array_equal(keys.cpu().numpy().view(np.uint64), sig), mode
+
+
 @pytest.mark.parametrize("exec_mode", ["batched", "plain"])
 def test_band_keys(lshb, oracle, corpus, exec_mode):
     off, tok = _small_corpus(corpus, n=500)
