@@ -91,3 +91,31 @@ def test_filter_sizing_matches_the_oracle(built, oracle):
     for bad in ((0, 0.1), (10, 0.0), (10, 1.0)):
         with pytest.raises(L.LSHBloomError):
             L.filter_sizing(*bad)
+
+
+def test_invalid_configurations_are_refused_before_any_device_work(built):
+    """lshbloom_create_ex validates the whole configuration first: each
+    violated rule gives LSHB_ERR_ARG and a message naming it, on a host with
+    or without a GPU."""
+    import numpy as np
+
+    import paper_2411_04257_gb300 as L
+    bad = [
+        (dict(P=0), "num_perm"), (dict(P=2000), "num_perm"), (dict(bands=0), "bands"),
+        (dict(bands=65, rows=1, P=128), "bands"), (dict(rows=0), "rows"),
+        (dict(P=100, bands=11, rows=11), "exceeds num_perm"), (dict(ngram=0), "ngram"),
+        (dict(ngram=65), "ngram"), (dict(n_expected=0), "n_expected"),
+        (dict(fp_rate=0.0), "fp_rate"), (dict(fp_rate=1.0), "fp_rate"),
+        (dict(item_shingles=8), "item_shingles"), (dict(fp_rate=1e-25), "exceeds 64"),
+        (dict(perm_a=np.ones(121, np.uint64), perm_b=np.full(121, 2**61, np.uint64)), "perm_b"),
+        (dict(perm_a=np.zeros(121, np.uint64), perm_b=np.zeros(121, np.uint64)), "perm_a"),
+    ]
+    for kw, word in bad:
+        P = kw.pop("P", 121)
+        bands = kw.pop("bands", 11)
+        rows = kw.pop("rows", 11)
+        with pytest.raises(L.LSHBloomError) as e:
+            L.LSHBloom(P, bands, rows, **kw)
+        assert e.value.status == -1 and word in str(e.value), (kw, str(e.value))
+    with pytest.raises(KeyError):
+        L.LSHBloom(121, 11, 11, bloom_layout="striped")
