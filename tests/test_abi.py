@@ -119,3 +119,15 @@ def test_invalid_configurations_are_refused_before_any_device_work(built):
         assert e.value.status == -1 and word in str(e.value), (kw, str(e.value))
     with pytest.raises(KeyError):
         L.LSHBloom(121, 11, 11, bloom_layout="striped")
+
+
+def test_optimal_br_matches_the_oracle_on_the_host(built, oracle):
+    """lshbloom_optimal_br is host code: (b, r) for thresholds and permutation
+    counts equal the oracle's tuner (Eqs. 1-2), including the paper's 9 bands
+    at T = 0.8, P = 128 and 42 x 6 at T = 0.5, P = 256."""
+    import paper_2411_04257_gb300 as L
+    assert L.optimal_br(0.8, 128) == (9, 13)
+    assert L.optimal_br(0.5, 256) == (42, 6)
+    for T in (0.3, 0.5, 0.65, 0.8, 0.9):
+        for P in (32, 64, 121, 128, 200):
+            assert L.optimal_br(T, P) == oracle.optimal_br(T, P), (T, P)
