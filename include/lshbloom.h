@@ -233,9 +233,11 @@ LSHB_API lshb_status lshbloom_band_keys(lshbloom_t *h, const uint64_t *offsets, 
  * own fixed-budget pool, or latency-critical loops where cudaMalloc's
  * device-wide synchronisation would stall other streams).  The paper has no
  * counterpart: this is a deployment variant of the same computation.
- * The intermediate signature matrix lives in a 16 MiB array compiled into
- * the library, which every GPU that loads the library holds until the
- * process exits; D * P * 4 bytes must fit in it (D <= 34663 at P = 121),
+ * With P <= 256 (one signature pass) the signature kernel writes the keys
+ * directly and no intermediate matrix exists.  With P > 256 the signature
+ * matrix lives in a 16 MiB array compiled into the library, which every GPU
+ * that loads the library holds until the process exits; D * P * 4 bytes must
+ * fit in it (D <= 8192 at P = 512, D <= 4096 at P = 1024), and
  * larger batches get LSHB_ERR_ARG with the limit in the message.
  * offsets, tokens, keys_out: device pointers (as lshbloom_band_keys;
  * keys_out is uint64[D][b]); work is ordered on `stream` (a cudaStream_t,

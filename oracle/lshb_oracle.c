@@ -613,14 +613,45 @@ static void or_set_bit(or_index *ix, uint32_t j, uint64_t q) {
 /* The stream of documents is processed strictly in order (Sec. 4.4.2: index
  * writes stay sequential so each document is judged against the ones before
  * it; Sec. 2.1 defines the decision against D_seen = {d_j | j < i}).
- * For document i:
+ * For document i with band keys keys[0 .. bands-1]:
  *   - its band keys are probed in their filters (Sec. 4.2); a band hits when
  *     all k probed bits are set (Sec. 2.4); the document is a duplicate when
  *     any band hits;
  *   - then it is inserted (Sec. 4.1): every probed bit is set.  Reading of
  *     Sec. 4.4.2: by default only documents found not to be duplicates are
  *     inserted; insert_all inserts every document.
- * The query comes before the insert, so a document never matches itself. */
+ * The query comes before the insert, so a document never matches itself.
+ * q is scratch for bands * k positions.  Returns the duplicate flag. */
+static int or_index_judge(or_index *ix, const uint64_t *keys, uint64_t *q) {
+    int dup = 0;
+    if (ix->layout == 2) {
+        or_keyset *sets = (or_keyset *)ix->sets;
+        for (uint32_t j = 0; j < ix->bands; ++j)
+            if (or_set_contains(&sets[j], keys[j])) dup = 1;
+        if (ix->insert_all || !dup)
+            for (uint32_t j = 0; j < ix->bands; ++j) or_set_add(&sets[j], keys[j]);
+        ix->docs_seen++;
+        return dup;
+    }
+    for (uint32_t j = 0; j < ix->bands; ++j) {
+        uint64_t *qj = q + (uint64_t)j * ix->k;
+        or_index_positions(ix, keys[j], j, qj);
+        int all_set = 1;
+        for (uint32_t u = 0; u < ix->k; ++u)
+            if (!or_get_bit(ix, j, qj[u])) all_set = 0;
+        if (all_set) dup = 1;
+    }
+    if (ix->insert_all || !dup) {
+        for (uint32_t j = 0; j < ix->bands; ++j)
+            for (uint32_t u = 0; u < ix->k; ++u)
+                or_set_bit(ix, j, q[(uint64_t)j * ix->k + u]);
+    }
+    ix->docs_seen++;
+    return dup;
+}
+
+/* A batch of D documents: signature (Sec. 2.2, 4.1), band keys (Sec. 4.1),
+ * then the stream decision above, one document after the other. */
 OR_API void or_index_dedup(or_index *ix, const uint64_t *offsets, const uint32_t *tokens,
                            uint64_t D, uint8_t *flags) {
     uint32_t *sig = (uint32_t *)malloc(sizeof(uint32_t) * ix->P);
@@ -630,34 +661,21 @@ OR_API void or_index_dedup(or_index *ix, const uint64_t *offsets, const uint32_t
         uint64_t L = offsets[i + 1] - offsets[i];
         or_signature(tokens + offsets[i], L, ix->ngram, ix->P, ix->a, ix->b, sig);
         or_band_keys_mode(sig, ix->bands, ix->rows, ix->band_key, keys);
-        int dup = 0;
-        if (ix->layout == 2) {
-            or_keyset *sets = (or_keyset *)ix->sets;
-            for (uint32_t j = 0; j < ix->bands; ++j)
-                if (or_set_contains(&sets[j], keys[j])) dup = 1;
-            flags[i] = (uint8_t)dup;
-            if (ix->insert_all || !dup)
-                for (uint32_t j = 0; j < ix->bands; ++j) or_set_add(&sets[j], keys[j]);
-            ix->docs_seen++;
-            continue;
-        }
-        for (uint32_t j = 0; j < ix->bands; ++j) {
-            uint64_t *qj = q + (uint64_t)j * ix->k;
-            or_index_positions(ix, keys[j], j, qj);
-            int all_set = 1;
-            for (uint32_t u = 0; u < ix->k; ++u)
-                if (!or_get_bit(ix, j, qj[u])) all_set = 0;
-            if (all_set) dup = 1;
-        }
-        flags[i] = (uint8_t)dup;
-        if (ix->insert_all || !dup) {
-            for (uint32_t j = 0; j < ix->bands; ++j)
-                for (uint32_t u = 0; u < ix->k; ++u)
-                    or_set_bit(ix, j, q[(uint64_t)j * ix->k + u]);
-        }
-        ix->docs_seen++;
+        flags[i] = (uint8_t)or_index_judge(ix, keys, q);
     }
     free(sig); free(keys); free(q);
+}
+
+/* The same stream decision fed with band keys already computed (row i of
+ * keys holds document i's bands keys[i*bands .. i*bands + bands-1]): the
+ * order-dependent half of the path, replayed alone.  A document's keys depend
+ * on that document only, so a caller may compute them in any order (or in
+ * parallel, with or_batch_band_keys) and get the flags of or_index_dedup. */
+OR_API void or_index_dedup_keys(or_index *ix, const uint64_t *keys, uint64_t D, uint8_t *flags) {
+    uint64_t *q = (uint64_t *)malloc(sizeof(uint64_t) * ix->k * ix->bands);
+    for (uint64_t i = 0; i < D; ++i)
+        flags[i] = (uint8_t)or_index_judge(ix, keys + i * ix->bands, q);
+    free(q);
 }
 
 /* Bloom filter alone (Sec. 2.4), for the false-positive closed-form pin:
@@ -723,4 +741,17 @@ OR_API void or_batch_shingle_hashes(const uint64_t *offsets, const uint32_t *tok
         for (uint64_t s = 0; s < S; ++s) h_out[o++] = or_shingle_hash(tokens + offsets[i] + s, w);
         counts[i] = S;
     }
+}
+
+/* Band keys of a CSR batch (Sec. 2.2, Sec. 4.1): signature then band keys,
+ * per document; keys_out is D x bands, row-major. */
+OR_API void or_batch_band_keys(const uint64_t *offsets, const uint32_t *tokens, uint64_t D,
+                               uint32_t n, uint32_t P, const uint64_t *a, const uint64_t *b,
+                               uint32_t bands, uint32_t rows, uint32_t mode, uint64_t *keys_out) {
+    uint32_t *sig = (uint32_t *)malloc(sizeof(uint32_t) * P);
+    for (uint64_t i = 0; i < D; ++i) {
+        or_signature(tokens + offsets[i], offsets[i + 1] - offsets[i], n, P, a, b, sig);
+        or_band_keys_mode(sig, bands, rows, mode, keys_out + i * bands);
+    }
+    free(sig);
 }

@@ -19,6 +19,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lshb_oracle.c")
+_SRC_THREADS = os.path.join(_HERE, "lshb_cpu_threads.c")
 _LIB = os.path.join(_HERE, "liblshb_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -27,12 +28,14 @@ P61 = (1 << 61) - 1
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, no vector intrinsics)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    """Compile the oracle and its threaded driver with gcc (plain -O2, no
+    vector intrinsics)."""
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_THREADS))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.run(
-            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fvisibility=hidden",
-             "-o", tmp, _SRC, "-lm"],
+            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fvisibility=hidden", "-pthread",
+             "-o", tmp, _SRC, _SRC_THREADS, "-lm"],
             check=True)
         os.replace(tmp, _LIB)
     return _LIB
@@ -82,6 +85,17 @@ def lib():
                                                  C.c_uint32]),
                 "or_index_destroy": (None, [C.c_void_p]),
                 "or_index_dedup": (None, [C.c_void_p, u64p, u32p, C.c_uint64, u8p]),
+                "or_index_dedup_keys": (None, [C.c_void_p, u64p, C.c_uint64, u8p]),
+                "or_batch_band_keys": (None, [u64p, u32p, C.c_uint64, C.c_uint32, C.c_uint32,
+                                              u64p, u64p, C.c_uint32, C.c_uint32, C.c_uint32,
+                                              u64p]),
+                "ort_batch_band_keys": (C.c_uint32, [u64p, u32p, C.c_uint64, C.c_uint32,
+                                                     C.c_uint32, u64p, u64p, C.c_uint32,
+                                                     C.c_uint32, C.c_uint32, u64p, C.c_uint32]),
+                "ort_index_dedup": (C.c_uint32, [C.c_void_p, u64p, u32p, C.c_uint64, u8p,
+                                                 C.c_uint32, C.c_uint32, u64p, u64p, C.c_uint32,
+                                                 C.c_uint32, C.c_uint32, C.c_uint32,
+                                                 C.c_uint64]),
                 "or_index_query_key": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint64]),
                 "or_index_insert_key": (None, [C.c_void_p, C.c_uint32, C.c_uint64]),
                 "or_index_insert_keys": (None, [C.c_void_p, C.c_uint32, u64p, C.c_uint64]),
@@ -194,6 +208,34 @@ def batch_signatures(offsets, tokens, n: int, a, b) -> np.ndarray:
     return out
 
 
+def host_threads() -> int:
+    """Host cores this process may run on."""
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except (AttributeError, OSError):
+        return max(1, os.cpu_count() or 1)
+
+
+def batch_band_keys(offsets, tokens, n: int, a, b, bands: int, rows: int, mode: int = 0,
+                    threads: int = 1) -> np.ndarray:
+    """Band keys (D x bands) of a CSR batch.  threads > 1 runs the unchanged
+    per-document oracle on several threads (lshb_cpu_threads.c)."""
+    off = _u64(offsets)
+    tok = _u32(tokens)
+    D = off.size - 1
+    out = np.zeros((max(D, 1), bands), np.uint64)
+    tt = tok if tok.size else np.zeros(1, np.uint32)
+    aa, bb = _u64(a), _u64(b)
+    if D > 0:
+        args = (_p(off, C.c_uint64), _p(tt, C.c_uint32), D, n, len(aa), _p(aa, C.c_uint64),
+                _p(bb, C.c_uint64), bands, rows, mode, _p(out, C.c_uint64))
+        if threads > 1:
+            lib().ort_batch_band_keys(*args, threads)
+        else:
+            lib().or_batch_band_keys(*args)
+    return out[:max(D, 0)]
+
+
 def batch_shingle_hashes(offsets, tokens, n: int):
     off = _u64(offsets)
     tok = _u32(tokens)
@@ -282,6 +324,7 @@ class OracleIndex:
             a, b = coefficients(seed, P)
         self.a, self.b = _u64(a), _u64(b)
         self.P, self.bands, self.rows, self.ngram = P, bands, rows, ngram
+        self.band_key = band_key
         self._h = lib().or_index_create(P, bands, rows, ngram, self.m, self.k,
                                         _p(self.a, C.c_uint64), _p(self.b, C.c_uint64),
                                         1 if insert_all else 0)
@@ -310,6 +353,34 @@ class OracleIndex:
             lib().or_index_dedup(self._h, _p(off, C.c_uint64), _p(tt, C.c_uint32), D,
                                  _p(flags, C.c_uint8))
         return flags[:max(D, 0)]
+
+    def dedup_keys(self, keys) -> np.ndarray:
+        """The stream decision alone, fed with band keys (D x bands)."""
+        k = _u64(keys).reshape(-1, self.bands)
+        D = k.shape[0]
+        flags = np.zeros(max(D, 1), np.uint8)
+        if D > 0:
+            lib().or_index_dedup_keys(self._h, _p(k, C.c_uint64), D, _p(flags, C.c_uint8))
+        return flags[:D]
+
+    def dedup_threaded(self, offsets, tokens, threads: int | None = None,
+                       block_docs: int = 65536):
+        """As dedup, with the band keys of each block of documents computed on
+        `threads` threads and the decisions taken in order (the paper's CPU
+        design, Sec. 4.4.2).  Returns (flags, threads used)."""
+        off = _u64(offsets)
+        tok = _u32(tokens)
+        D = off.size - 1
+        flags = np.zeros(max(D, 1), np.uint8)
+        tt = tok if tok.size else np.zeros(1, np.uint32)
+        used = 1
+        if D > 0:
+            used = lib().ort_index_dedup(self._h, _p(off, C.c_uint64), _p(tt, C.c_uint32), D,
+                                         _p(flags, C.c_uint8), self.ngram, self.P,
+                                         _p(self.a, C.c_uint64), _p(self.b, C.c_uint64),
+                                         self.bands, self.rows, self.band_key,
+                                         threads or host_threads(), block_docs)
+        return flags[:max(D, 0)], int(used)
 
     def query_key(self, j: int, key: int) -> bool:
         return bool(lib().or_index_query_key(self._h, j, key))

@@ -4,9 +4,11 @@
 // that hand all GPU memory to their own pool with a fixed budget, and
 // latency-critical loops where cudaMalloc's implicit synchronisation of the
 // whole device would stall unrelated streams.  This entry point computes the
-// same band keys as lshbloom_band_keys, but keeps the intermediate signature
-// matrix in a fixed array compiled into the library instead of in memory it
-// allocates.  The caller still provides the input and output buffers.
+// same band keys as lshbloom_band_keys without allocating: with more than 256
+// permutations (several signature passes) the intermediate signature matrix
+// lives in a fixed array compiled into the library; with one pass the
+// signature kernel writes the keys directly.  The caller still provides the
+// input and output buffers.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -59,13 +61,16 @@ extern "C" LSHB_API lshb_status lshbloom_band_keys_static(lshbloom_t *h, const u
     if (!h) return fail(LSHB_ERR_ARG, "NULL handle");
     if (D == 0) return LSHB_OK;
     if (!offsets || !tokens || !keys_out) return fail(LSHB_ERR_ARG, "NULL pointer with D > 0");
-    const uint64_t need = D * (uint64_t)h->P * 4;
-    if (need > kStaticSigBytes)
+    // More than one signature pass (P > 256) keeps the signature matrix in the
+    // fixed array.  Compared by division: D * P * 4 can wrap around 2^64.
+    const bool single = h->passes.size() == 1;
+    const uint64_t max_docs = kStaticSigBytes / (4ull * h->P);
+    if (!single && D > max_docs)
         return fail(LSHB_ERR_ARG,
-                    "lshbloom_band_keys_static: %llu documents x %u permutations need %llu bytes "
-                    "of signature scratch; the fixed array holds %zu (at most %llu documents)",
-                    (unsigned long long)D, h->P, (unsigned long long)need, kStaticSigBytes,
-                    (unsigned long long)(kStaticSigBytes / (4ull * h->P)));
+                    "lshbloom_band_keys_static: %llu documents x %u permutations need more "
+                    "signature scratch than the fixed array holds (%zu bytes, at most %llu "
+                    "documents)",
+                    (unsigned long long)D, h->P, kStaticSigBytes, (unsigned long long)max_docs);
     if (!is_device_pointer(offsets) || !is_device_pointer(tokens) || !is_device_pointer(keys_out))
         return fail(LSHB_ERR_ARG, "lshbloom_band_keys_static takes device pointers only");
     std::lock_guard<std::mutex> lock(h->mu);
@@ -103,7 +108,10 @@ extern "C" LSHB_API lshb_status lshbloom_band_keys_static(lshbloom_t *h, const u
     a.P = h->P;
     a.bands = h->bands;
     a.rows = h->rows;
-    a.sig_out = sig;
+    // One pass: the kernel's epilogue writes the band keys itself, with no
+    // signature matrix in between.
+    a.sig_out = single ? nullptr : sig;
+    a.keys_out = single ? keys_out : nullptr;
     const int ngt = ngram_template(h->ngram);
     for (const SigPass &ps : h->passes) {
         a.p0 = ps.p0;
@@ -114,7 +122,9 @@ extern "C" LSHB_API lshb_status lshbloom_band_keys_static(lshbloom_t *h, const u
         else e = launch_sig_ng0(ps.ppl, a, s);
         if (e != cudaSuccess) return cuda_fail(e, "signature kernel");
     }
-    if ((e = launch_band_keys(sig, h->P, h->bands, h->rows, h->cfg.band_key, D, keys_out, s)) != cudaSuccess)
+    if (!single &&
+        (e = launch_band_keys(sig, h->P, h->bands, h->rows, h->cfg.band_key, D, keys_out, s)) !=
+            cudaSuccess)
         return cuda_fail(e, "band-key kernel");
     return LSHB_OK;
 }

@@ -1,20 +1,23 @@
-"""Parity at the workloads' full sizes, in the launch configuration bench.py
-times (batched form, whole batch per call, default chunking).
+"""Bit-exact parity at the workloads' full sizes, in the launch configuration
+bench.py times (batched form, whole batch per call, default chunking).
 
-The oracle cannot replay a million-document stream in test time, so:
-  * sampled documents: the oracle computes their band keys one by one, and
-    the keys the timed path used must equal them exactly (the longest
-    documents, split over many work items, are always in the sample);
-  * every document: a document with an exact band match against an earlier
-    inserted document (the MinHashLSH bucket rule) must be flagged, and
-    flags without one must be Bloom false positives (fill^k, ~0 here);
-  * the plain one-kernel-per-stage form gives the same flags."""
+For every document the oracle computes the band keys (shingling, SHA-1,
+MinHash, band sums: Sec. 2.2, Sec. 4.1) from its tokens; those are per
+document, so the host's cores share the documents (the unchanged
+single-threaded oracle on each thread).  The keys the GPU judged with must
+equal them for every document.  The oracle then replays the stream decision
+(Sec. 2.1, Sec. 4.2, Sec. 4.4.2) from its own keys, one document after the
+other, and the GPU's flags must equal its flags for every document and the
+GPU's filters its filters, byte for byte.  The CPU tests check that this
+replay equals the oracle's one-document loop."""
 import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
+
+P, BANDS, ROWS, NGRAM = 121, 11, 11, 5
 
 
 @pytest.fixture(scope="module")
@@ -26,69 +29,49 @@ def lshb():
     return L
 
 
-def exact_bucket_hits(keys, flags):
-    """hit[i]: some band of doc i has the same key as an earlier doc that was
-    inserted (flag 0, insert-non-duplicates rule)."""
-    D, b = keys.shape
-    inserted = (flags == 0).astype(np.int64)
-    idx = np.arange(D)
-    hit = np.zeros(D, bool)
-    for j in range(b):
-        order = np.lexsort((idx, keys[:, j]))
-        ks = keys[order, j]
-        ins = inserted[order]
-        start = np.ones(D, bool)
-        start[1:] = ks[1:] != ks[:-1]
-        grp = np.cumsum(start) - 1
-        before = np.cumsum(ins) - ins
-        hit[order] |= (before - before[start][grp]) > 0
-    return hit
-
-
-def _check(lshb, oracle, spec, n_expected, calls=1, sample=200, seed=0):
+def _check_exact(lshb, oracle, spec, n_expected, calls=1):
+    """Deduplicate `spec` in `calls` calls on the GPU and on the oracle;
+    compare every band key, every flag and every filter byte."""
     from synth import gpu as sgpu
     gen = sgpu.DeviceCorpus(spec)
-    ix = lshb.LSHBloom(121, 11, 11, n_expected=n_expected, fp_rate=1e-5)
+    ix = lshb.LSHBloom(P, BANDS, ROWS, n_expected=n_expected, fp_rate=1e-5)
+    ref = oracle.OracleIndex(P, BANDS, ROWS, n_expected=n_expected, fp_rate=1e-5)
+    assert (ix.m, ix.k) == (ref.m, ref.k)
+    threads = oracle.host_threads()
     per = spec.n_docs // calls
-    flags, keys, lens, samples = [], [], [], []
-    rnd = np.random.default_rng(seed)
+    flags = []
     for c in range(calls):
         off, tok = gen.generate(c * per, per)
         f, k = ix.dedup_keys(off, tok)
         torch.cuda.synchronize()
         off_h = off.cpu().numpy().view(np.uint64)
-        L = np.diff(off_h)
-        pick = set(rnd.choice(per, size=min(sample // calls, per), replace=False).tolist())
-        pick |= set(np.argsort(L)[-3:].tolist())        # the longest: split over many items
-        k_h = k.cpu().numpy().view(np.uint64)
-        for d in sorted(pick):
-            t = tok[int(off_h[d]):int(off_h[d + 1])].cpu().numpy().view(np.uint32)
-            samples.append((t, k_h[d]))
-        flags.append(f.cpu().numpy())
-        keys.append(k_h)
-        lens.append(L)
-        del off, tok
-    flags = np.concatenate(flags)
-    keys = np.concatenate(keys)
-    a, b = oracle.coefficients(1, 121)
-    for t, want_keys in samples:
-        sig = oracle.signature(t, 5, a, b)
-        assert np.array_equal(oracle.band_keys(sig, 11, 11), want_keys)
-    hit = exact_bucket_hits(keys, flags)
-    assert np.all(flags[hit] == 1), "an exact band match was not flagged"
-    extra = int(np.sum((flags == 1) & ~hit))
-    assert extra <= 2, extra
-    return ix, flags, gen
+        tok_h = tok.cpu().numpy().view(np.uint32)
+        got_keys = k.cpu().numpy().view(np.uint64)
+        got = f.cpu().numpy()
+        del off, tok, f, k
+        want_keys = oracle.batch_band_keys(off_h, tok_h, NGRAM, ref.a, ref.b, BANDS, ROWS,
+                                           threads=threads)
+        del tok_h
+        bad = np.nonzero((got_keys != want_keys).any(axis=1))[0]
+        assert bad.size == 0, f"call {c}: band keys differ for {bad.size} documents: {bad[:8]}"
+        want = ref.dedup_keys(want_keys)
+        diff = np.nonzero(got != want)[0]
+        assert diff.size == 0, f"call {c}: flags differ for {diff.size} documents: {diff[:8]}"
+        flags.append(got)
+    for j in range(BANDS):
+        assert np.array_equal(ix.filter_bytes(j), ref.filter_bytes(j)), f"filter {j} differs"
+    ref.close()
+    return ix, np.concatenate(flags), gen
 
 
 def test_pes2o_shaped_1m(lshb, oracle):
     from synth import corpus
     spec = corpus.pes2o_shaped(n_docs=1_000_000)
-    ix, flags, gen = _check(lshb, oracle, spec, 39_000_000)
+    ix, flags, gen = _check_exact(lshb, oracle, spec, 39_000_000)
     assert 100_000 < flags.sum() < 200_000
     # the plain form agrees on the whole batch
     off, tok = gen.generate(0, spec.n_docs)
-    ixp = lshb.LSHBloom(121, 11, 11, n_expected=39_000_000, fp_rate=1e-5, exec_mode="plain")
+    ixp = lshb.LSHBloom(P, BANDS, ROWS, n_expected=39_000_000, fp_rate=1e-5, exec_mode="plain")
     assert np.array_equal(ixp.dedup(off, tok).cpu().numpy(), flags)
     ixp.close()
     # and so does the batch from page-locked host memory (the bench's e2e leg:
@@ -99,19 +82,22 @@ def test_pes2o_shaped_1m(lshb, oracle):
     h_tok.copy_(tok)
     del off, tok
     torch.cuda.empty_cache()
-    ixh = lshb.LSHBloom(121, 11, 11, n_expected=39_000_000, fp_rate=1e-5)
+    ixh = lshb.LSHBloom(P, BANDS, ROWS, n_expected=39_000_000, fp_rate=1e-5)
     assert np.array_equal(np.asarray(ixh.dedup(h_off, h_tok)), flags)
     st = ixh.stats()
     assert st["host_read_bytes"] == h_tok.numel() * 4 and st["h2d_bytes"] == 0
-    for j in (0, 10):
+    for j in range(BANDS):
         assert np.array_equal(ixh.filter_bytes(j), ix.filter_bytes(j))
+    ixh.close()
+    ix.close()
 
 
 def test_pareto_batched_8m(lshb, oracle):
     from synth import corpus
     spec = corpus.pareto_batched(n_docs=8_000_000)
-    _, flags, _ = _check(lshb, oracle, spec, 39_000_000, sample=400)
+    ix, flags, _ = _check_exact(lshb, oracle, spec, 39_000_000)
     assert flags.sum() > 300_000
+    ix.close()
 
 
 def test_billion_stream_prefix_three_calls(lshb, oracle):
@@ -120,5 +106,6 @@ def test_billion_stream_prefix_three_calls(lshb, oracle):
     n = 1e9 (11 x 3 GB), three calls continuing one stream."""
     from synth import corpus
     spec = corpus.billion_stream(n_docs=3_000_000)
-    _, flags, _ = _check(lshb, oracle, spec, 1_000_000_000, calls=3, sample=300)
+    ix, flags, _ = _check_exact(lshb, oracle, spec, 1_000_000_000, calls=3)
     assert flags.sum() > 20_000
+    ix.close()
