@@ -50,6 +50,13 @@
  * buffers.  The caller owns all buffers it passes; the handle owns its
  * filters and scratch.
  *
+ * Ordering of device buffers: the synchronous calls (lshbloom_dedup,
+ * lshbloom_dedup_keys, lshbloom_signatures, lshbloom_band_keys,
+ * lshbloom_shingle_hashes) run on the handle's own stream after all work
+ * enqueued before the call on the legacy default stream; device inputs
+ * written on another stream must be complete before the call (or pass that
+ * stream to lshbloom_dedup_async).
+ *
  * CSR batches: document d of a batch of D documents is
  * tokens[offsets[d] .. offsets[d+1]-1]; offsets has D+1 non-decreasing
  * entries (offsets[0] need not be 0); tokens holds uint32 word hashes.

@@ -51,6 +51,15 @@ def _out(n_items, row, np_dtype, torch_dtype, like_cuda_tensor):
     return a.ctypes.data, a
 
 
+def _after_current_stream(t) -> None:
+    """The synchronous C calls wait for the legacy default stream only; a CUDA
+    tensor made on another torch stream must be complete before the call."""
+    import torch
+    st = torch.cuda.current_stream(t.device)
+    if st.cuda_stream != 0:
+        st.synchronize()
+
+
 _LAYOUTS = {"standard": 0, "blocked": 1, "exact": 2}
 
 
@@ -120,9 +129,11 @@ class LSHBloom:
         return self._h.value
 
     # -- the path ---------------------------------------------------------------
-    def _inputs(self, offsets, tokens):
+    def _inputs(self, offsets, tokens, sync=True):
         po, ko, co = _arg(offsets, np.uint64, ["uint64", "int64"])
         pt, kt, ct = _arg(tokens, np.uint32, ["uint32", "int32"])
+        if sync and (co or ct):
+            _after_current_stream(kt if ct else ko)
         D = (ko.shape[0] if hasattr(ko, "shape") else len(ko)) - 1
         like = kt if ct else None
         return po, pt, max(D, 0), like, (ko, kt)
@@ -150,7 +161,7 @@ class LSHBloom:
         """As dedup, device tensors only, ordered on `stream` (torch stream or
         raw cudaStream_t; default the current torch stream)."""
         import torch
-        po, pt, D, like, keep = self._inputs(offsets, tokens)
+        po, pt, D, like, keep = self._inputs(offsets, tokens, sync=False)
         pf, fl = _out(D, None, np.uint8, "uint8", like)
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -174,7 +185,7 @@ class LSHBloom:
         """Band keys through lshbloom_band_keys_static: no allocation inside
         the library (device tensors only; `out` may be preallocated)."""
         import torch
-        po, pt, D, like, keep = self._inputs(offsets, tokens)
+        po, pt, D, like, keep = self._inputs(offsets, tokens, sync=False)
         if out is None:
             pk, keys = _out(D, self.bands, np.uint64, "uint64", like)
         else:

@@ -204,6 +204,7 @@ lshbloom::~lshbloom() {
         if (ev_t[i]) cudaEventDestroy(ev_t[i]);
     for (int i = 0; i < 2; ++i)
         if (ev_p[i]) cudaEventDestroy(ev_p[i]);
+    if (ev_order) cudaEventDestroy(ev_order);
     if (counters) cudaFree(counters);
     if (host_counters) cudaFreeHost(host_counters);
     if (stream) cudaStreamDestroy(stream);
@@ -347,6 +348,7 @@ lshb_status lshb::init_handle(lshbloom *h, const lshb_config *cfg) {
     }
     for (int i = 0; i < 3; ++i) CK(cudaEventCreate(&h->ev_t[i]));
     for (int i = 0; i < 2; ++i) CK(cudaEventCreate(&h->ev_p[i]));
+    CK(cudaEventCreateWithFlags(&h->ev_order, cudaEventDisableTiming));
     const size_t fbytes = (size_t)h->bands * h->words_per_filter * 4;
     cudaError_t e = cudaMalloc(&h->filters, fbytes);
     if (e != cudaSuccess) {
@@ -450,13 +452,15 @@ bool lshb::is_device_pointer(const void *p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-// Host copy of the batch offsets (validated: non-decreasing).
+// Host copy of the batch offsets (validated: non-decreasing); device offsets
+// are read on stream s, after the work already enqueued there.
 lshb_status lshb::host_offsets(lshbloom *h, const uint64_t *offsets, uint64_t D, bool dev,
-                               std::vector<uint64_t> &out) {
+                               std::vector<uint64_t> &out, cudaStream_t s) {
+    (void)h;
     out.resize(D + 1);
     if (dev) {
-        CK(cudaMemcpyAsync(out.data(), offsets, (D + 1) * 8, cudaMemcpyDeviceToHost, h->stream));
-        CK(cudaStreamSynchronize(h->stream));
+        CK(cudaMemcpyAsync(out.data(), offsets, (D + 1) * 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
     } else {
         memcpy(out.data(), offsets, (D + 1) * 8);
     }
@@ -767,8 +771,15 @@ static lshb_status run_batch(lshbloom *h, const uint64_t *offsets, const uint32_
         }
     }
     cudaStream_t s = user_stream ? user_stream : h->stream;
+    // A synchronous call runs on the handle's own (non-blocking) stream: order
+    // it after everything already enqueued on the legacy default stream, where
+    // a caller's device inputs are usually produced.
+    if (!user_stream && (off_dev || tok_dev || out_dev)) {
+        CK(cudaEventRecord(h->ev_order, cudaStreamLegacy));
+        CK(cudaStreamWaitEvent(s, h->ev_order, 0));
+    }
     std::vector<uint64_t> off;
-    lshb_status st = host_offsets(h, offsets, D, off_dev, off);
+    lshb_status st = host_offsets(h, offsets, D, off_dev, off, s);
     if (st != LSHB_OK) return st;
     if (tok_in_place && job == Job::Dedup) h->host_read_bytes += (off[D] - off[0]) * 4;
     if (job == Job::Dedup && h->cfg.exec_mode == LSHB_EXEC_BATCHED && h->passes.size() == 1) {

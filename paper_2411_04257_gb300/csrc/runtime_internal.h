@@ -90,6 +90,7 @@ struct lshbloom {
     double t_sig_ms = 0.0, t_bloom_ms = 0.0;
     uint64_t sig_chunks = 0;
     cudaEvent_t ev_p[2] = {nullptr, nullptr};  // bracket the probe kernel (one-kernel-per-stage form)
+    cudaEvent_t ev_order = nullptr;  // orders a synchronous call after the legacy default stream
     double t_probe_ms = 0.0;
     uint64_t probe_sectors = 0;                // band-key probes issued by that kernel
     bool probe_pending = false;
@@ -116,7 +117,7 @@ const void *mapped_host_pointer(const void *p);
 const void *host_read_pointer(bool pageable_access, const void *p);
 bool device_reads_pageable(int device);
 lshb_status host_offsets(lshbloom *h, const uint64_t *offsets, uint64_t D, bool dev,
-                         std::vector<uint64_t> &out);
+                         std::vector<uint64_t> &out, cudaStream_t s);
 void plan_chunks(const lshbloom *h, const std::vector<uint64_t> &off, bool bound_tokens,
                  std::vector<std::pair<uint64_t, uint64_t>> &chunks,
                  uint64_t first_tokens = 0);

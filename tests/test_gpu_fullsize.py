@@ -42,6 +42,7 @@ def _check_exact(lshb, oracle, spec, n_expected, calls=1):
     flags = []
     for c in range(calls):
         off, tok = gen.generate(c * per, per)
+        torch.cuda.synchronize()
         f, k = ix.dedup_keys(off, tok)
         torch.cuda.synchronize()
         off_h = off.cpu().numpy().view(np.uint64)
