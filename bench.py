@@ -10,7 +10,16 @@ does the same work.
 Prints one JSON line (rank 0).  `value` is docs/s of the batched form with
 inputs resident in HBM; `plain` is the one-kernel-per-stage form on the same
 batch; `e2e` is the same metric through lshbloom_dedup with pinned host
-buffers, host<->device copies inside the timed region.
+buffers, host<->device copies inside the timed region.  Beside them:
+`roofline` (the persistent signature kernel against the integer-multiply
+peak, and against the measured ceiling of its own arithmetic),
+`roofline_probe` (the Bloom probe kernel against the copy peak and the
+measured random-sector rates), `index_variants` (blocked filters, exact
+band-key sets, weighted band keys), `serve`, `configs` (the 10k-document,
+8M-document Pareto and billion-document configurations, each with its own
+clocks and CPU baselines), `cpu_baseline` (the oracle, one thread, bounded
+sample), `cpu_threaded` (the oracle on all host cores, the paper's CPU
+design) and `device_peaks` (microbench/peaks.cu).
 
 --impl reference times the CPU oracle (single thread) on a bounded sample of
 the same workload.
@@ -50,9 +59,7 @@ def _config(name, world):
             "rows": ROWS, "ngram": NGRAM, "n_expected": nexp, "fp_rate": fp,
             "l2": "inputs larger than L2 (tokens %.1f GB)" % (T * 4 / 1e9),
             "parallelism": f"replicas{world}"}
-SM_COUNT = 152
 IMAD_PER_SM_CLK = 64        # 32-bit integer multiply(-add) results per SM per clock
-SM_MAX_MHZ = 2070.0
 IMAD_PER_PERMHASH = 4       # two 32x32->64 products (lo and hi halves) per (a*h + b)
 
 
@@ -65,16 +72,14 @@ IMAD_PER_PERMHASH = 4       # two 32x32->64 products (lo and hi halves) per (a*h
 # reports null.
 _CSRC = "paper_2411_04257_gb300/csrc/"
 _TRAFFIC = {
-    "k_batched": {"bytes_per_doc": 55150.0,
+    "k_batched": {"bytes_per_doc": None,
                   "sources": ["batched_kernels.cuh", "sig_kernels.cuh", "lshb_device.cuh",
                               "bloom_kernels.cuh", "lshb_internal.h"],
-                  "sha256": "06bf28f566345357508f1d79d4ac909645fdc3424ee6235892570456c0f16c6e",
-                  "profile": "profiles/dram_traffic_pes2o100k.md"},
-    "k_probe_mark": {"bytes_per_doc": 24807.0,
-                     "sources": ["bloom_kernels.cu", "bloom_kernels.cuh", "lshb_device.cuh",
-                                 "lshb_internal.h"],
-                     "sha256": "650c63af607d56747a5b54743d5448edaa77d0756779e491c03b7bc076ee33d4",
-                     "profile": "profiles/dram_traffic_pes2o100k.md"},
+                  "sha256": None, "profile": None},
+    "k_probe": {"bytes_per_doc": None,
+                "sources": ["bloom_kernels.cu", "bloom_kernels.cuh", "lshb_device.cuh",
+                            "lshb_internal.h"],
+                "sha256": None, "profile": None},
 }
 
 
@@ -101,9 +106,40 @@ def _sources_sha256(files, read=None):
 def _traffic(kernel, docs_per_launch):
     """Measured DRAM bytes of one launch of `kernel`, or None once it changed."""
     t = _TRAFFIC[kernel]
-    if not docs_per_launch or _sources_sha256(t["sources"]) != t["sha256"]:
+    if not docs_per_launch or not t["sha256"] or _sources_sha256(t["sources"]) != t["sha256"]:
         return None
     return t["bytes_per_doc"] * docs_per_launch
+
+
+def _device_peaks(local):
+    """Measured issue rates, random-sector rates and the signature stage's own
+    ceiling on this GPU (microbench/peaks.cu), or the error that stopped them."""
+    try:
+        from microbench import peaks
+        return peaks.measure(local)
+    except Exception as e:  # measurement support, not the product path
+        return {"error": repr(e)}
+
+
+def _sm_max_mhz(clocks):
+    """Maximum SM clock: sampled from nvidia-smi during the timed steps, else
+    the generated peaks file."""
+    if clocks and clocks.get("sm_max_mhz"):
+        return float(clocks["sm_max_mhz"])
+    peaks, _ = _measured_peaks()
+    return float(peaks.get("sm_max_mhz", 2070.0))
+
+
+def _best_gather(g):
+    """(load form, GB/s) of the fastest 4-byte random-sector read form."""
+    if not g:
+        return None, None
+    forms = {k: v for k, v in g.items() if isinstance(v, dict) and "atom" not in k
+             and "whole sector" not in k}
+    if not forms:
+        return None, None
+    k = max(forms, key=lambda x: forms[x]["gbs"])
+    return k, forms[k]["gbs"]
 
 
 def _measured_peaks():
@@ -115,23 +151,35 @@ def _measured_peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
-def _probe_roofline(st, standard_layout=True):
-    """The stand-alone probe kernel of the plain form: each probe of a band key
-    reads one 32-byte sector of a filter that does not fit in L2.  One probe
-    launch per chunk; `traffic` is known for the standard layout only."""
+def _probe_roofline(st, dev_peaks, standard_layout=True):
+    """The band-major probe kernel k_probe (one launch per chunk, both forms):
+    each probe of a band key addresses one 32-byte sector of its band's
+    filter; band by band, one 116.8 MB filter at a time, the working set is
+    L2-sized.  `peak` is the measured copy bandwidth; the measured random
+    4-byte sector reads over a 4 GiB (DRAM) and a 64 MiB (L2) buffer bracket
+    what random sectors can attain."""
     if not st or not st["probe_ms"] or not st["probe_sectors"]:
         return None
     peaks, src = _measured_peaks()
     gbs = st["probe_sectors"] * 32 / (st["probe_ms"] / 1e3) / 1e9
     docs_per_launch = st["docs"] / max(1, st["sig_chunks"])
-    traffic = _traffic("k_probe_mark", docs_per_launch) if standard_layout else None
-    return {"bound": "hbm", "kernel": "k_probe_mark (plain form)", "achieved": gbs,
-            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
-            "traffic": traffic, "algorithmic_bytes_per_launch":
-                st["probe_sectors"] * 32 / max(1, st["sig_chunks"]),
-            "peak_source": f"hbm_gbs, {src}",
-            "algorithmic_bytes": "32 B per addressed sector: b*k = 187 per document "
-                                 "(standard layout), b = 11 (blocked layout)"}
+    traffic = _traffic("k_probe", docs_per_launch) if standard_layout else None
+    out = {"bound": "hbm", "kernel": "k_probe (band-major)", "achieved": gbs,
+           "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+           "traffic": traffic, "algorithmic_bytes_per_launch":
+               st["probe_sectors"] * 32 / max(1, st["sig_chunks"]),
+           "launch_ms": st["probe_ms"] / max(1, st["sig_chunks"]),
+           "peak_source": f"hbm_gbs, {src}",
+           "algorithmic_bytes": "32 B per addressed sector: b*k = 187 per document "
+                                "(standard layout), b = 11 (blocked layout)"}
+    if dev_peaks and "gather_dram" in dev_peaks:
+        fd, gd = _best_gather(dev_peaks["gather_dram"])
+        fl, gl = _best_gather(dev_peaks["gather_l2"])
+        out["random_sector_peaks"] = {"dram_4gib": {"gbs": gd, "load": fd},
+                                      "l2_64mib": {"gbs": gl, "load": fl}}
+        out["frac_of_random_dram"] = gbs / gd if gd else None
+        out["frac_of_random_l2"] = gbs / gl if gl else None
+    return out
 
 
 def _clocks_rejected(c):
@@ -242,26 +290,6 @@ class Clocks:
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][1]),
                 "reasons": sorted(reasons), "samples": len(sm)}
-
-
-def _cpu_baseline(spec, nexp, fp, target_s=12.0):
-    """The oracle as it stands, single-threaded, on a prefix of the workload."""
-    from oracle import oracle
-    from synth import corpus
-    t = corpus.build_tables(spec)
-    n = 16
-    while True:
-        off, tok = corpus.generate(spec, 0, n, tables=t)
-        ix = oracle.OracleIndex(P, BANDS, ROWS, n_expected=nexp, fp_rate=fp, ngram=NGRAM)
-        t0 = time.perf_counter()
-        ix.dedup(off, tok)
-        dt = time.perf_counter() - t0
-        ix.close()
-        if dt > target_s / 4 or n >= spec.n_docs:
-            break
-        n = min(spec.n_docs, max(n * 2, int(n * target_s / max(dt, 1e-3) / 2)))
-    return {"value": n / dt, "unit": "docs/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {n} docs of the workload ({int(off[-1])} tokens), {dt:.1f} s"}
 
 
 def run_reference(args):
@@ -390,6 +418,187 @@ def _time_steps(fn, steps, warmup, stream, sync, on_start=None):
     return ev[0].elapsed_time(ev[1]) / 1e3
 
 
+def _timed_mode(ix, off, tok, stream, steps, warmup, sync, local, dev):
+    """Timed steps of one index (each step clears the filters and deduplicates
+    the batch); a run under a slowdown is measured once more."""
+    import torch
+
+    def step():
+        ix.reset()
+        with torch.cuda.stream(stream):
+            ix.dedup_async(off, tok, stream=stream)
+
+    rejected = None
+    for attempt in range(2):
+        s0 = {}
+        with Clocks(local) as ck:
+            dt = _time_steps(step, steps, warmup, stream, sync,
+                             on_start=lambda: s0.update(ix.stats()))
+        clocks = ck.summary()
+        s1 = ix.stats()
+        if attempt == 0 and _any_rank(_clocks_rejected(clocks), dev):
+            rejected = clocks          # measured under a slowdown: once more
+            continue
+        break
+    if rejected is not None:
+        clocks["rejected_first_run"] = rejected
+    stage = {"sig_ms": s1["sig_ms"] - s0["sig_ms"], "bloom_ms": s1["bloom_ms"] - s0["bloom_ms"],
+             "sig_chunks": s1["sig_chunks"] - s0["sig_chunks"],
+             "probe_ms": s1["probe_ms"] - s0["probe_ms"],
+             "probe_sectors": s1["probe_sectors"] - s0["probe_sectors"],
+             "launches": s1["kernel_launches"] - s0["kernel_launches"],
+             "resolve_rounds": s1["resolve_rounds"] - s0["resolve_rounds"],
+             "uncertain_docs": s1["uncertain_docs"] - s0["uncertain_docs"]}
+    return dt, clocks, stage
+
+
+def _shingles(off):
+    L = off[1:] - off[:-1]
+    import torch
+    return int(torch.where(L >= NGRAM, L - NGRAM + 1, (L > 0).to(L.dtype)).sum().item())
+
+
+def _cpu_threaded(off_h, tok_h, nexp, fp, what):
+    """The paper's CPU design on the oracle (band keys on all host cores, the
+    stream decisions in order on one), on a prefix of the workload."""
+    from oracle import oracle
+    D = off_h.size - 1
+    ix = oracle.OracleIndex(P, BANDS, ROWS, n_expected=nexp, fp_rate=fp, ngram=NGRAM)
+    t0 = time.perf_counter()
+    flags, used = ix.dedup_threaded(off_h, tok_h, threads=oracle.host_threads())
+    dt = time.perf_counter() - t0
+    ix.close()
+    return {"value": D / dt, "unit": "docs/s", "cores": used,
+            "kind": "oracle, threaded: band keys of each 65,536-document block on all "
+                    "threads, then the stream decisions in order on one",
+            "sample": f"{what}: first {D} docs ({int(off_h[-1] - off_h[0])} tokens), {dt:.1f} s",
+            "dups": int(flags.sum())}
+
+
+def _cpu_oracle(off_h, tok_h, nexp, fp, target_s, what):
+    """The oracle as it stands, one thread, on the first documents of
+    off_h/tok_h, the count grown until the run takes about target_s/4 .. target_s."""
+    from oracle import oracle
+    D = off_h.size - 1
+    n = min(16, D)
+    while True:
+        ix = oracle.OracleIndex(P, BANDS, ROWS, n_expected=nexp, fp_rate=fp, ngram=NGRAM)
+        t0 = time.perf_counter()
+        ix.dedup(off_h[:n + 1], tok_h)
+        dt = time.perf_counter() - t0
+        ix.close()
+        if dt > target_s / 4 or n >= D:
+            break
+        n = min(D, max(n * 2, int(n * target_s / max(dt, 1e-3) / 2)))
+    return {"value": n / dt, "unit": "docs/s", "cores": 1, "kind": "oracle",
+            "sample": f"{what}: first {n} docs ({int(off_h[n] - off_h[0])} tokens), {dt:.1f} s"}
+
+
+def _config_record(name, factory, n_docs, nexp, local, dev, stream, sync, steps, warmup,
+                   cpu, threaded_docs, plain=False):
+    """One BASELINE configuration on one GPU: its batch resident in HBM, the
+    batched form timed over `steps` steps (each clears the filters), and the
+    CPU baselines on its first documents."""
+    import dataclasses
+
+    import numpy as np
+
+    from paper_2411_04257_gb300 import LSHBloom
+    from synth import corpus
+    from synth import gpu as sgpu
+    spec = dataclasses.replace(getattr(corpus, factory)(), n_docs=n_docs)
+    off, tok = sgpu.DeviceCorpus(spec, dev).generate(0, n_docs)
+    sync()
+    S = _shingles(off)
+    rec = {"workload": f"{name}: {n_docs} docs, {int(off[-1].item())} tokens, {S} shingles",
+           "n_expected": nexp, "fp_rate": 1e-5, "steps": steps, "warmup": warmup}
+    for mode in (["batched", "plain"] if plain else ["batched"]):
+        ix = LSHBloom(P, BANDS, ROWS, n_expected=nexp, fp_rate=1e-5, ngram=NGRAM,
+                      exec_mode=mode, device=local)
+        dt, clocks, st = _timed_mode(ix, off, tok, stream, steps, warmup, sync, local, dev)
+        ix.reset()
+        flags = ix.dedup_async(off, tok, stream=stream)
+        sync()
+        r = {"docs_per_s": n_docs * steps / dt, "shingle_hashes_per_s": S * P * steps / dt,
+             "ms_per_step": 1e3 * dt / steps,
+             "stage_ms_per_step": {"signature": st["sig_ms"] / steps,
+                                   "bloom": st["bloom_ms"] / steps,
+                                   "probe": st["probe_ms"] / steps},
+             "resolve_sweeps_per_step": st["resolve_rounds"] / steps,
+             "uncertain_docs_per_step": st["uncertain_docs"] / steps,
+             "gpu_launches_per_step": st["launches"] / steps,
+             "dups_per_step": int(flags.sum().item()), "clocks": clocks}
+        rec[mode] = r
+        ix.close()
+    if cpu:
+        n = min(n_docs, threaded_docs)
+        off_h = off[:n + 1].cpu().numpy().view(np.uint64)
+        tok_h = tok[:int(off_h[-1])].cpu().numpy().view(np.uint32)
+        del off, tok
+        rec["cpu_baseline"] = _cpu_oracle(off_h, tok_h, nexp, 1e-5, 10.0, name)
+        rec["cpu_threaded"] = _cpu_threaded(off_h, tok_h, nexp, 1e-5, name)
+    return rec
+
+
+def _billion_record(local, dev, sync, chunk_docs, n_docs, cpu):
+    """The billion-document stream in full: documents generated per chunk on
+    the device from the counter-based generator (never stored), each chunk
+    deduplicated by one call continuing one stream into filters sized for
+    n = 1e9 (11 x 3.0 GB).  Throughput counts the dedup calls (CUDA events on
+    their stream); the wall time with generation is reported beside it."""
+    import numpy as np
+    import torch
+
+    from paper_2411_04257_gb300 import LSHBloom
+    from synth import corpus
+    from synth import gpu as sgpu
+    spec = corpus.billion_stream(n_docs=n_docs)
+    gen = sgpu.DeviceCorpus(spec, dev)
+    ix = LSHBloom(P, BANDS, ROWS, n_expected=1_000_000_000, fp_rate=1e-5, ngram=NGRAM,
+                  device=local)
+    stream = torch.cuda.Stream(dev)
+    dedup_s, docs, shingles, tokens, dups = 0.0, 0, 0, 0, 0
+    s0 = ix.stats()
+    t0 = time.perf_counter()
+    with Clocks(local) as ck:
+        for d0 in range(0, n_docs, chunk_docs):
+            D = min(chunk_docs, n_docs - d0)
+            off, tok = gen.generate(d0, D)
+            shingles += _shingles(off)
+            tokens += int(tok.numel())
+            sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            flags = ix.dedup_async(off, tok, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            dedup_s += e0.elapsed_time(e1) / 1e3
+            docs += D
+            dups += int(flags.sum().item())
+            del off, tok, flags
+    wall = time.perf_counter() - t0
+    s1 = ix.stats()
+    ix.close()
+    rec = {"workload": f"billion_stream: {docs} docs, {tokens} tokens, {shingles} shingles "
+                       f"(generated on the device per chunk of {chunk_docs} docs)",
+           "n_expected": 1_000_000_000, "fp_rate": 1e-5, "chunks": (n_docs + chunk_docs - 1)
+           // chunk_docs, "docs_per_s": docs / dedup_s, "shingle_hashes_per_s":
+               shingles * P / dedup_s, "dedup_s": dedup_s, "wall_s_with_generation": wall,
+           "stage_s": {"signature": (s1["sig_ms"] - s0["sig_ms"]) / 1e3,
+                       "bloom": (s1["bloom_ms"] - s0["bloom_ms"]) / 1e3},
+           "dups": dups, "clocks": ck.summary()}
+    if cpu:
+        off, tok = gen.generate(0, 1_000_000)
+        sync()
+        off_h = off.cpu().numpy().view(np.uint64)
+        tok_h = tok.cpu().numpy().view(np.uint32)
+        del off, tok
+        rec["cpu_baseline"] = _cpu_oracle(off_h, tok_h, 1_000_000_000, 1e-5, 10.0,
+                                          "billion_stream")
+        rec["cpu_threaded"] = _cpu_threaded(off_h, tok_h, 1_000_000_000, 1e-5, "billion_stream")
+    return rec
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -403,19 +612,19 @@ def run_ours(args):
     from paper_2411_04257_gb300 import LSHBloom
     from synth import gpu as sgpu
 
+    dev_peaks = None if args.skip_peaks else _device_peaks(local)
     spec, nexp, fp = _spec(args.workload, rank)
     gen = sgpu.DeviceCorpus(spec, dev)
     off, tok = gen.generate(0, spec.n_docs)
     torch.cuda.synchronize()
     D = spec.n_docs
     T = int(off[-1].item())
-    L = (off[1:] - off[:-1])
-    S = torch.where(L >= NGRAM, L - NGRAM + 1, (L > 0).to(L.dtype))
-    shingles = int(S.sum().item())
+    shingles = _shingles(off)
     permhashes = shingles * P
     if rank == 0 and (D, T, shingles) != (WORKLOADS[args.workload][1], *WORKLOADS[args.workload][4:]):
         raise RuntimeError(f"generated corpus ({D} docs, {T} tokens, {shingles} shingles) differs "
                            f"from the workload table")
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
 
     stream = torch.cuda.Stream(dev)
 
@@ -425,13 +634,10 @@ def run_ours(args):
             dist.barrier()
 
     results = {}
-    launches = {}
     stage = {}
-    item_shingles = None
     modes = ["batched", "plain"] if not args.skip_plain else ["batched"]
-    if args.variants:
-        modes += ["batched/blocked", "plain/blocked", "batched/exact", "plain/exact",
-                  "batched/weighted"]
+    if not args.skip_variants:
+        modes += ["batched/blocked", "batched/exact", "batched/weighted"]
     index_bytes = {}
     for mode in modes:
         variant = mode.split("/")[1] if "/" in mode else "standard"
@@ -441,50 +647,56 @@ def run_ours(args):
                       band_key="weighted" if variant == "weighted" else "sum")
         st0 = ix.stats()
         index_bytes[layout] = st0["filter_bytes"] * st0["bands"]
-
-        def step():
-            ix.reset()
-            with torch.cuda.stream(stream):
-                ix.dedup_async(off, tok, stream=stream)
-
-        rejected = None
-        for attempt in range(2):
-            s0 = {}
-            with Clocks(local) as ck:
-                dt = _time_steps(step, args.steps, args.warmup, stream, barrier_sync,
-                                 on_start=lambda: s0.update(ix.stats()))
-            clocks = ck.summary()
-            s1 = ix.stats()
-            if attempt == 0 and _any_rank(_clocks_rejected(clocks), dev):
-                rejected = clocks          # measured under a slowdown: once more
-                continue
-            break
-        if rejected is not None:
-            clocks["rejected_first_run"] = rejected
-        if mode == "batched":
-            item_shingles = s1["item_shingles"]
-        launches[mode] = s1["kernel_launches"] - s0["kernel_launches"]
-        stage[mode] = {"sig_ms": s1["sig_ms"] - s0["sig_ms"],
-                       "bloom_ms": s1["bloom_ms"] - s0["bloom_ms"],
-                       "sig_chunks": s1["sig_chunks"] - s0["sig_chunks"],
-                       "probe_ms": s1["probe_ms"] - s0["probe_ms"],
-                       "probe_sectors": s1["probe_sectors"] - s0["probe_sectors"],
-                       "docs": D * args.steps}
-        dt, docs = reduce_over_ranks(dt, float(D * args.steps), dev)
-        _, ph = reduce_over_ranks(dt, float(permhashes * args.steps), dev)
+        # the layout variants are context: fewer steps
+        steps = args.steps if "/" not in mode else min(args.steps, 5)
+        warmup = args.warmup if "/" not in mode else min(args.warmup, 2)
+        dt, clocks, st = _timed_mode(ix, off, tok, stream, steps, warmup, barrier_sync, local, dev)
+        st["docs"] = D * steps
+        st["steps"] = steps
+        stage[mode] = st
+        dt, docs = reduce_over_ranks(dt, float(D * steps), dev)
+        _, ph = reduce_over_ranks(dt, float(permhashes * steps), dev)
         ix.reset()
         flags = ix.dedup_async(off, tok, stream=stream)
         torch.cuda.synchronize()
-        results[mode] = {"seconds": dt, "docs_per_s": docs / dt, "shingle_hashes_per_s": ph / dt,
-                         "clocks": clocks, "dups_per_step": int(flags.sum().item())}
+        results[mode] = {"seconds": dt, "steps": steps, "docs_per_s": docs / dt,
+                         "shingle_hashes_per_s": ph / dt, "clocks": clocks,
+                         "dups_per_step": int(flags.sum().item()),
+                         "item_shingles": ix.stats()["item_shingles"]}
         ix.close()
 
-    # --- dominant kernel: the signature stage, timed with CUDA events on its
-    # launching stream inside the timed steps (library stage timers) --------
+    # --- dominant kernel: the signature stage (persistent kernel), timed with
+    # CUDA events on its launching stream inside the timed steps ------------
     sb = stage["batched"]
     sig_s = sb["sig_ms"] / 1e3 / args.steps          # per step
     achieved_imad = IMAD_PER_PERMHASH * permhashes / sig_s
-    peak_imad = SM_COUNT * IMAD_PER_SM_CLK * SM_MAX_MHZ * 1e6
+    clocks_b = results["batched"]["clocks"]
+    sm_max = _sm_max_mhz(clocks_b)
+    peak_imad = sms * IMAD_PER_SM_CLK * sm_max * 1e6
+    roofline = {"bound": "alu", "kernel": "k_batched (SHA-1 + MinHash + band keys)",
+                "achieved": achieved_imad / 1e12, "peak": peak_imad / 1e12,
+                "unit": "T int-mul/s", "frac": achieved_imad / peak_imad,
+                "traffic": _traffic("k_batched", D * args.steps / max(1, sb["sig_chunks"])),
+                "launch_ms": sb["sig_ms"] / max(1, sb["sig_chunks"]),
+                "launches_per_step": sb["sig_chunks"] / args.steps,
+                "perm_hashes_per_s": permhashes / sig_s,
+                "peak_source": f"{sms} SMs (device) x {IMAD_PER_SM_CLK} IMAD/clk x "
+                               f"{sm_max:.0f} MHz (nvidia-smi maximum)"}
+    if dev_peaks and "issue" in dev_peaks and dev_peaks["issue"]:
+        iss = dev_peaks["issue"]
+        roofline["measured_issue_rates"] = {k: v["ops_per_s"] for k, v in iss.items()}
+        roofline["frac_of_measured_mad_lo"] = achieved_imad / iss["mad.lo.u32"]["ops_per_s"]
+    if dev_peaks and dev_peaks.get("ceiling"):
+        both = dev_peaks["ceiling"].get("sha1 + fold")
+        fold = dev_peaks["ceiling"].get("fold (P=121, PPL=4)")
+        sha = dev_peaks["ceiling"].get("sha1 5-gram windows")
+        roofline["ceiling"] = {
+            "what": "the same SHA-1 window hash and MinHash fold from registers and shared "
+                    "memory, no global memory (microbench/peaks.cu)",
+            "sha1_plus_fold_perm_hashes_per_s": both["perm_hashes_per_s"] if both else None,
+            "fold_only_perm_hashes_per_s": fold["perm_hashes_per_s"] if fold else None,
+            "sha1_only_shingles_per_s": sha["shingles_per_s"] if sha else None,
+            "frac": (permhashes / sig_s) / both["perm_hashes_per_s"] if both else None}
 
     # --- end to end through host buffers --------------------------------------
     e2e = None
@@ -541,17 +753,41 @@ def run_ours(args):
                "clocks": e2e_clocks}
         del h_tok
 
+    # CPU baselines read the first documents of the resident batch
+    cpu = cpu_thr = None
+    if rank == 0 and not args.skip_cpu:
+        n_thr = min(D, args.threaded_docs)
+        off_h = off[:n_thr + 1].cpu().numpy().view(np.uint64)
+        tok_h = tok[:int(off_h[-1])].cpu().numpy().view(np.uint32)
+        cpu = _cpu_oracle(off_h, tok_h, nexp, fp, 12.0, args.workload)
+        cpu_thr = _cpu_threaded(off_h, tok_h, nexp, fp, args.workload)
+        del off_h, tok_h
+
     serve = None
+    del off, tok
+    torch.cuda.empty_cache()
     if not args.skip_serve:
-        del off, tok
-        torch.cuda.empty_cache()
         serve = _serve_bench(local)
+
+    # the other configurations: parity cases, measured here as sub-records
+    configs = None
+    if not args.skip_configs:
+        configs = {}
+        cpu_cfg = rank == 0 and not args.skip_cpu
+        configs["plain_10k"] = _config_record("plain_10k", "plain_10k", 10_000, 10_000, local, dev,
+                                              stream, barrier_sync, 50, 5, cpu_cfg, 10_000,
+                                              plain=True)
+        configs["pareto_8m"] = _config_record("pareto_8m", "pareto_batched", 8_000_000, 39_000_000,
+                                              local, dev, stream, barrier_sync, 5, 2, cpu_cfg,
+                                              1_000_000, plain=True)
+        torch.cuda.empty_cache()
+        configs["billion_stream"] = _billion_record(local, dev, barrier_sync, args.billion_chunk,
+                                                    args.billion_docs, cpu_cfg)
 
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return 0
-    cpu = None if args.skip_cpu else _cpu_baseline(spec, nexp, fp)
     b = results["batched"]
     line = {
         "metric": METRIC,
@@ -567,25 +803,23 @@ def run_ours(args):
         "dups_per_step": b["dups_per_step"],
         "clocks": b["clocks"],
         "e2e": e2e,
-        "gpu_launches": launches["batched"],
-        "roofline": {"bound": "alu", "kernel": "signature (SHA-1 + MinHash + band keys)",
-                     "achieved": achieved_imad / 1e12, "peak": peak_imad / 1e12,
-                     "unit": "T int-mul/s", "frac": achieved_imad / peak_imad,
-                     "traffic": _traffic("k_batched", D * args.steps / max(1, sb["sig_chunks"])),
-                     "launch_ms": 1e3 * sb["sig_ms"] / 1e3 / max(1, sb["sig_chunks"]),
-                     "launches_per_step": sb["sig_chunks"] / args.steps,
-                     "perm_hashes_per_s": permhashes / sig_s,
-                     "peak_source": "152 SMs x 64 IMAD/clk x 2070 MHz (derived)"},
-        "stage_ms_per_step": {m: {"signature": v["sig_ms"] / args.steps,
-                                  "bloom": v["bloom_ms"] / args.steps} for m, v in stage.items()},
-        "roofline_probe": _probe_roofline(stage.get("plain")),
+        "gpu_launches": stage["batched"]["launches"],
+        "roofline": roofline,
+        "stage_ms_per_step": {m: {"signature": v["sig_ms"] / v["steps"],
+                                  "bloom": v["bloom_ms"] / v["steps"],
+                                  "probe": v["probe_ms"] / v["steps"],
+                                  "resolve_sweeps": v["resolve_rounds"] / v["steps"]}
+                              for m, v in stage.items()},
+        "roofline_probe": _probe_roofline(stage.get("batched"), dev_peaks),
         "index_variants": ({lay: {"batched_docs_per_s": results[f"batched/{lay}"]["docs_per_s"],
-                                  "plain_docs_per_s": results[f"plain/{lay}"]["docs_per_s"],
+                                  "steps": results[f"batched/{lay}"]["steps"],
                                   "dups_per_step": results[f"batched/{lay}"]["dups_per_step"],
                                   "index_bytes": index_bytes[lay],
                                   "bloom_stage_ms_per_step":
-                                      stage[f"batched/{lay}"]["bloom_ms"] / args.steps,
-                                  "roofline_probe": _probe_roofline(stage[f"plain/{lay}"], False)}
+                                      stage[f"batched/{lay}"]["bloom_ms"]
+                                      / stage[f"batched/{lay}"]["steps"],
+                                  "roofline_probe": _probe_roofline(stage[f"batched/{lay}"],
+                                                                    dev_peaks, False)}
                             for lay in ("blocked", "exact")} | {
                                "standard": {"index_bytes": index_bytes["standard"],
                                             "dups_per_step": b["dups_per_step"],
@@ -594,13 +828,18 @@ def run_ours(args):
                                # standard filters, weighted band keys (beyond the paper)
                                "weighted_band_keys": {
                                    "batched_docs_per_s": results["batched/weighted"]["docs_per_s"],
+                                   "steps": results["batched/weighted"]["steps"],
                                    "dups_per_step": results["batched/weighted"]["dups_per_step"],
                                    "bloom_stage_ms_per_step":
-                                       stage["batched/weighted"]["bloom_ms"] / args.steps}}
-                           if args.variants else None),
+                                       stage["batched/weighted"]["bloom_ms"]
+                                       / stage["batched/weighted"]["steps"]}}
+                           if not args.skip_variants else None),
         "serve": serve,
-        "item_shingles": item_shingles,
+        "configs": configs,
+        "item_shingles": b["item_shingles"],
         "cpu_baseline": cpu,
+        "cpu_threaded": cpu_thr,
+        "device_peaks": dev_peaks,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -620,9 +859,16 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-serve", action="store_true")
-    ap.add_argument("--variants", action="store_true",
-                    help="also measure the blocked filter layout, the exact band-key index "
-                         "and weighted band keys")
+    ap.add_argument("--skip-variants", action="store_true",
+                    help="skip the blocked filter layout, the exact band-key index and "
+                         "weighted band keys")
+    ap.add_argument("--skip-configs", action="store_true",
+                    help="skip the 10k, 8M Pareto and billion-document configurations")
+    ap.add_argument("--skip-peaks", action="store_true", help="skip the peak microbenchmarks")
+    ap.add_argument("--threaded-docs", type=int, default=100_000,
+                    help="documents of the workload the threaded CPU baseline runs")
+    ap.add_argument("--billion-docs", type=int, default=1_000_000_000)
+    ap.add_argument("--billion-chunk", type=int, default=4_000_000)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -224,6 +224,16 @@ LSHB_API lshb_status lshbloom_dedup_keys(lshbloom_t *h, const uint64_t *offsets,
                                          const uint32_t *tokens, uint64_t D, uint8_t *flags_out,
                                          uint64_t *keys_out);
 
+/* The Bloom-index half of lshbloom_dedup (Sec. 4.1, Sec. 4.2, Sec. 4.4.2) on
+ * band keys computed elsewhere: documents 0 .. D-1 with band keys
+ * keys[d*b .. d*b + b-1] (host or device uint64[D][b], row-major; any 64-bit
+ * values) are judged in order against all earlier documents of this handle
+ * and inserted by the insert rule, exactly as lshbloom_dedup judges the keys
+ * it computes.  flags_out: host or device uint8[D], 1 = duplicate.  D = 0 is
+ * a no-op.  Errors: ERR_ARG (NULL pointer with D > 0), ERR_OOM, ERR_CUDA. */
+LSHB_API lshb_status lshbloom_dedup_from_keys(lshbloom_t *h, const uint64_t *keys, uint64_t D,
+                                              uint8_t *flags_out);
+
 /* MinHash signatures of D documents (Sec. 2.2, Sec. 4.1), without touching the
  * filters.  sig_out: host or device uint32[D][P], row-major.  Errors as for
  * lshbloom_dedup. */
@@ -271,7 +281,10 @@ LSHB_API lshb_status lshbloom_shingle_hashes(lshbloom_t *h, const uint64_t *offs
 LSHB_API lshb_status lshbloom_coefficients(const lshbloom_t *h, uint64_t *a_out, uint64_t *b_out);
 
 /* Copy filter `band` to host memory: ceil(m/8) bytes, bit q of the filter at
- * byte q/8, bit q%8 (least significant first). */
+ * byte q/8, bit q%8 (least significant first).  EXACT_KEYS: the band's table
+ * as uint64 slots (stats filter_bytes bytes): cap key slots (cap a power of
+ * two, 2^64-1 = empty), then one slot that is 0 when the key 2^64-1 is in the
+ * set (2^64-1 otherwise), then 15 empty padding slots. */
 LSHB_API lshb_status lshbloom_filter_bytes(lshbloom_t *h, uint32_t band, uint8_t *host_out);
 
 /* Clear every filter and the document counters. */

@@ -1,9 +1,11 @@
 """Measured peaks for the rooflines of the LSHBloom kernels (see peaks.cu).
 
 measure(device) returns, on one GPU:
-  gather:  random 32-byte-sector reads over a buffer far larger than L2, as
-           GB/s of the sectors addressed (32 B each), per load form; random
-           4-byte atomic ORs (sectors/s); whole sectors read by 8 lanes;
+  gather_dram, gather_l2:
+           random 32-byte-sector reads over a 4 GiB buffer (far larger than
+           L2) and over a 64 MiB one (L2-resident), as GB/s of the sectors
+           addressed (32 B each), per load form; random 4-byte atomic ORs
+           (sectors/s); whole sectors read by 8 lanes;
   issue:   operations per second of mad.wide.u32, mad.lo.u32 and four ALU
            operations (eight independent chains per thread, all SMs);
   ceiling: shingles/s and perm-hashes/s of the library's SHA-1 window hash
@@ -75,28 +77,36 @@ def _best(f, reps=3):
     return best
 
 
-def measure(device: int = 0, gather_log2_sectors: int = 27, quick: bool = False) -> dict:
-    """All peaks on `device` (the current CUDA device must be `device`)."""
-    import numpy as np
+def _gather(L, sms, device, log2_sectors, per):
     import torch
-    L = lib()
-    props = torch.cuda.get_device_properties(device)
-    sms = props.multi_processor_count
-    out = {"sms": sms, "gather": {}, "issue": {}, "ceiling": {}}
-    nsect = 1 << gather_log2_sectors
+    nsect = 1 << log2_sectors
     buf = torch.zeros(nsect * 8, dtype=torch.int32, device=f"cuda:{device}")
     threads = sms * 2048
-    per = 128 if quick else 512
+    out = {"buffer_bytes": nsect * 32}
     for mode, name in GATHER_MODES.items():
         L.mb_gather(buf.data_ptr(), nsect - 1, threads, 8, mode, 7)          # warm-up
         ms = _best(lambda: L.mb_gather(buf.data_ptr(), nsect - 1, threads, per, mode, 1))
         acc = threads * per
         sectors = acc / 8 if mode == 7 else acc                          # mode 7: 8 lanes per sector
-        out["gather"][name] = {"sectors_per_s": sectors / (ms / 1e3),
-                               "gbs": sectors * 32 / (ms / 1e3) / 1e9, "ms": ms}
-    out["gather"]["buffer_bytes"] = nsect * 32
+        out[name] = {"sectors_per_s": sectors / (ms / 1e3),
+                     "gbs": sectors * 32 / (ms / 1e3) / 1e9, "ms": ms}
     del buf
     torch.cuda.empty_cache()
+    return out
+
+
+def measure(device: int = 0, quick: bool = False) -> dict:
+    """All peaks on `device` (the current CUDA device must be `device`):
+    random sectors over a 4 GiB buffer (DRAM) and over a 64 MiB one (L2)."""
+    import numpy as np
+    import torch
+    L = lib()
+    props = torch.cuda.get_device_properties(device)
+    sms = props.multi_processor_count
+    out = {"sms": sms, "issue": {}, "ceiling": {}}
+    per = 128 if quick else 512
+    out["gather_dram"] = _gather(L, sms, device, 27, per)
+    out["gather_l2"] = _gather(L, sms, device, 21, per)
     blocks = sms * 8
     iters = 2000 if quick else 20000
     for kind, name in ISSUE_KINDS.items():

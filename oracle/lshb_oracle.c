@@ -511,13 +511,15 @@ OR_API or_index *or_index_create(uint32_t P, uint32_t bands, uint32_t rows, uint
  * applied to band keys, i.e. the index without Bloom false positives.  One
  * open-addressing set per band, doubled when half full. */
 typedef struct {
-    uint64_t *slot; /* ~0 = empty (band keys are sums of r 32-bit values < 2^58) */
+    uint64_t *slot; /* ~0 = empty */
     uint64_t cap, used;
+    int has_max;    /* the key 2^64 - 1, which the empty marker cannot hold */
 } or_keyset;
 
 static uint64_t or_set_home(uint64_t key, uint64_t cap) { return or_mix64(key) & (cap - 1); }
 
 static int or_set_contains(const or_keyset *s, uint64_t key) {
+    if (key == ~0ull) return s->has_max;
     for (uint64_t i = or_set_home(key, s->cap);; i = (i + 1) & (s->cap - 1)) {
         if (s->slot[i] == key) return 1;
         if (s->slot[i] == ~0ull) return 0;
@@ -530,6 +532,7 @@ static void or_set_grow(or_keyset *s) {
     or_keyset t;
     t.cap = s->cap * 2;
     t.used = 0;
+    t.has_max = s->has_max;
     t.slot = (uint64_t *)malloc(sizeof(uint64_t) * t.cap);
     memset(t.slot, 0xff, sizeof(uint64_t) * t.cap);
     for (uint64_t i = 0; i < s->cap; ++i)
@@ -539,6 +542,10 @@ static void or_set_grow(or_keyset *s) {
 }
 
 static void or_set_add(or_keyset *s, uint64_t key) {
+    if (key == ~0ull) {
+        s->has_max = 1;
+        return;
+    }
     if (2 * (s->used + 1) > s->cap) or_set_grow(s);
     for (uint64_t i = or_set_home(key, s->cap);; i = (i + 1) & (s->cap - 1)) {
         if (s->slot[i] == key) return;
@@ -584,6 +591,10 @@ OR_API uint64_t or_index_exact_keys(const or_index *ix, uint32_t j, uint64_t *ou
             if (n < cap) out[n] = s->slot[i];
             n++;
         }
+    if (s->has_max) {
+        if (n < cap) out[n] = ~0ull;
+        n++;
+    }
     return n;
 }
 

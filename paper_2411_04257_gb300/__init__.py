@@ -157,6 +157,19 @@ class LSHBloom:
         check(lib().lshbloom_dedup_keys(self._h, po, pt, D, pf, pk))
         return fl, keys
 
+    def dedup_from_keys(self, keys):
+        """Flags of documents given by their band keys (D x bands, uint64 or
+        int64, host or device), judged and inserted in order."""
+        pk, kk, ck = _arg(keys, np.uint64, ["uint64", "int64"])
+        if ck:
+            _after_current_stream(kk)
+        D = kk.shape[0] if kk.ndim == 2 else kk.shape[0] // self.bands
+        if kk.ndim == 2 and kk.shape[1] != self.bands:
+            raise ValueError(f"keys must have {self.bands} columns")
+        pf, fl = _out(D, None, np.uint8, "uint8", kk if ck else None)
+        check(lib().lshbloom_dedup_from_keys(self._h, pk, D, pf))
+        return fl
+
     def dedup_async(self, offsets, tokens, stream=None):
         """As dedup, device tensors only, ordered on `stream` (torch stream or
         raw cudaStream_t; default the current torch stream)."""
@@ -252,6 +265,17 @@ class LSHBloom:
         out = np.zeros(self._dims()[5], np.uint8)
         check(lib().lshbloom_filter_bytes(self._h, band, out.ctypes.data))
         return out
+
+    def exact_keys(self, band: int) -> np.ndarray:
+        """Sorted band keys stored in band `band`'s table (exact-key layout):
+        the table's cap key slots, then the slot recording the key 2^64-1,
+        then 15 padding slots."""
+        t = self.filter_bytes(band).view(np.uint64)
+        cap = t.size - 16
+        keys = t[:cap][t[:cap] != np.uint64(2**64 - 1)]
+        if t[cap] == 0:
+            keys = np.append(keys, np.uint64(2**64 - 1))
+        return np.sort(keys)
 
     def reset(self) -> None:
         check(lib().lshbloom_reset(self._h))

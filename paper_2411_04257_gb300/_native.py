@@ -63,6 +63,7 @@ _SIGS = {
     "lshbloom_dedup": (C.c_int, [_VP, _VP, _VP, C.c_uint64, _VP]),
     "lshbloom_dedup_async": (C.c_int, [_VP, _VP, _VP, C.c_uint64, _VP, _VP]),
     "lshbloom_dedup_keys": (C.c_int, [_VP, _VP, _VP, C.c_uint64, _VP, _VP]),
+    "lshbloom_dedup_from_keys": (C.c_int, [_VP, _VP, C.c_uint64, _VP]),
     "lshbloom_signatures": (C.c_int, [_VP, _VP, _VP, C.c_uint64, _VP]),
     "lshbloom_band_keys": (C.c_int, [_VP, _VP, _VP, C.c_uint64, _VP]),
     "lshbloom_shingle_hashes": (C.c_int, [_VP, _VP, _VP, C.c_uint64, _VP]),

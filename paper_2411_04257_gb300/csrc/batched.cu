@@ -4,8 +4,8 @@
 // Per chunk the graph runs: per-document item counts, a scan, the item ->
 // document map, the persistent kernel (SHA-1 + MinHash for its item; a
 // document split over several items merges its minima with atomicMin and the
-// last item to finish forms the band keys and probes the filters), then the
-// classification of the Bloom stage.  The per-chunk pointers and sizes are
+// last item to finish forms the band keys), then the probes and the
+// classification of the Bloom stage, band by band.  The per-chunk pointers and sizes are
 // copied into a device-side parameter block at the start of the graph, so one
 // instantiated graph serves every chunk of a handle.  In-batch order
 // resolution and the insert follow on the host-driven path (they depend on how
@@ -36,6 +36,7 @@ struct BatchedState {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // bracket the persistent kernel
+    cudaEvent_t ev2 = nullptr;                  // end of the probe kernel (starts at ev1)
     cudaStream_t cap_stream = nullptr;          // private stream for graph capture
 
     void drop_graph() {
@@ -52,6 +53,7 @@ struct BatchedState {
         if (dyn_host) cudaFreeHost(dyn_host);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
+        if (ev2) cudaEventDestroy(ev2);
         if (cap_stream) cudaStreamDestroy(cap_stream);
     }
 };
@@ -126,12 +128,7 @@ static BatchArgs make_args(lshbloom *h, BatchedState *b) {
     a.npc = ps.npc;
     a.bands = h->bands;
     a.rows = h->rows;
-    a.k = h->k;
-    a.layout = h->layout;
     a.band_key = h->cfg.band_key;
-    a.m_bits = h->m;
-    a.words_per_filter = h->words_per_filter;
-    a.filters = h->filters;
     a.item_count = (uint32_t *)b->item_count.ptr;
     a.item_start = (uint64_t *)b->item_start.ptr;
     a.block_sums = (uint64_t *)b->block_sums.ptr;
@@ -141,21 +138,11 @@ static BatchArgs make_args(lshbloom *h, BatchedState *b) {
     a.sig_partial = (uint32_t *)b->sig_partial.ptr;
     a.queue = (unsigned long long *)(h->counters + C_QUEUE);
     a.keys = (uint64_t *)h->buf(B_KEYS).ptr;
-    a.miss = (uint64_t *)h->buf(B_MISS).ptr;
     a.cand = (uint64_t *)h->buf(B_CAND).ptr;
     a.prehit = (uint8_t *)h->buf(B_PREHIT).ptr;
-    a.sketch1 = (uint32_t *)h->buf(B_SKETCH1).ptr;
-    a.sketch2 = (uint32_t *)h->buf(B_SKETCH2).ptr;
     a.error = h->counters + C_ERROR;
     a.c = ps.c;
     return a;
-}
-
-static uint32_t sketch_log2_for(lshbloom *h, uint64_t D) {
-    const uint64_t marks = std::max<uint64_t>(D * h->bands * h->k * 8, 1ull << 16);
-    uint32_t lg = 16;
-    while ((1ull << lg) < marks && lg < h->sketch_log2_cap) ++lg;
-    return lg;
 }
 
 // Everything before the host-side resolution, for the chunk described by the
@@ -163,12 +150,12 @@ static uint32_t sketch_log2_for(lshbloom *h, uint64_t D) {
 static lshb_status enqueue_front(lshbloom *h, BatchedState *b, BatchArgs a, bool with_bloom,
                                  cudaStream_t s, bool time_kernel) {
     const uint64_t dcap = b->dcap;
-    a.sketch_log2 = sketch_log2_for(h, dcap);
+    BloomArgs A = bloom_args(h, dcap, dcap);
+    A.D_dev = &b->dyn->D;
     BCK(cudaMemcpyAsync(b->dyn, b->dyn_host, sizeof(DynParams), cudaMemcpyHostToDevice, s));
-    BCK(cudaMemsetAsync(h->counters, 0, 64, s));
-    const uint64_t sbytes = (1ull << a.sketch_log2) / 8;
-    BCK(cudaMemsetAsync(a.sketch1, 0, sbytes, s));
-    BCK(cudaMemsetAsync(a.sketch2, 0, sbytes, s));
+    BCK(cudaMemsetAsync(h->counters, 0, kChunkCounterBytes, s));
+    if (with_bloom)
+        BCK(cudaMemsetAsync(A.sketch, 0, (uint64_t)h->bands * (A.sketch_cells / 16) * 4, s));
     const unsigned nb = (unsigned)((dcap + kScanBlock - 1) / kScanBlock);
     unsigned pg = (unsigned)std::min<uint64_t>((dcap + 255) / 256, 16384);
     k_batch_prepare<<<pg ? pg : 1, 256, 0, s>>>(a);
@@ -191,12 +178,12 @@ static lshb_status enqueue_front(lshbloom *h, BatchedState *b, BatchArgs a, bool
     BCK(launch_k_batched(ngram_template(h->ngram), h->passes[0].ppl, a, b->grid, s));
     if (time_kernel) BCK(cudaEventRecordWithFlags(b->ev1, s, rec_flags));
     if (with_bloom) {
-        BloomArgs A = bloom_args(h, dcap);
-        A.D_dev = &b->dyn->D;
-        A.sketch_bits_log2 = a.sketch_log2;
-        BCK(launch_classify(A, (uint32_t *)h->buf(B_BLOCKCNT).ptr, h->counters + C_NU,
+        BCK(launch_probe(A, dcap, s));
+        if (time_kernel) BCK(cudaEventRecordWithFlags(b->ev2, s, rec_flags));
+        BCK(launch_classify(A, dcap, (uint32_t *)h->buf(B_BLOCKCNT).ptr, h->counters + C_NU,
                             (uint32_t *)h->buf(B_ULIST).ptr, s));
-        BCK(cudaMemcpyAsync(h->host_counters, h->counters, 64, cudaMemcpyDeviceToHost, s));
+        BCK(cudaMemcpyAsync(h->host_counters, h->counters, kChunkCounterBytes,
+                            cudaMemcpyDeviceToHost, s));
     }
     return LSHB_OK;
 }
@@ -209,6 +196,7 @@ static lshb_status ensure_state(lshbloom *h, uint64_t dcap, uint64_t tcap) {
         BCK(cudaMallocHost(&b->dyn_host, sizeof(DynParams)));
         BCK(cudaEventCreate(&b->ev0));
         BCK(cudaEventCreate(&b->ev1));
+        BCK(cudaEventCreate(&b->ev2));
         BCK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
     }
     if (dcap > b->dcap) {
@@ -357,20 +345,22 @@ lshb_status run_batched(lshbloom *h, const uint64_t *offsets, const uint32_t *to
         *b->dyn_host = dp;
         BCK(cudaEventRecord(h->ev_t[0], s));
         BCK(cudaGraphLaunch(b->exec, s));
-        count_launch(10);  // prepare, 3 scan, expand, persistent, 4 classify kernels
+        count_launch(11);  // prepare, 3 scan, expand, persistent, probe, 4 classify kernels
         BCK(cudaEventRecord(h->ev_t[1], s));
         // Prefetch the next chunk's tokens only now, while this chunk computes:
         // a copy call that blocks the host then no longer idles the GPU.
         if (!tok_dev && ci + 1 < chunks.size() && (st = issue_copy(ci + 1)) != LSHB_OK) return st;
         BCK(cudaStreamSynchronize(s));
         if (!tok_dev && (st = stage_copy_done(h, (int)(ci & 1))) != LSHB_OK) return st;
-        float ms_k7 = 0.f;
+        float ms_k7 = 0.f, ms_probe = 0.f;
         BCK(cudaEventElapsedTime(&ms_k7, b->ev0, b->ev1));
+        BCK(cudaEventElapsedTime(&ms_probe, b->ev1, b->ev2));
+        h->t_probe_ms += ms_probe;
+        h->probe_sectors += Dn * h->bands * probe_sectors_per_key(h);
         if (keys_out)
             BCK(cudaMemcpyAsync(keys_out + lo * h->bands, h->buf(B_KEYS).ptr, Dn * h->bands * 8,
                                 keys_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
-        BloomArgs A = bloom_args(h, Dn);
-        A.sketch_bits_log2 = sketch_log2_for(h, b->dcap);
+        BloomArgs A = bloom_args(h, Dn, b->dcap);
         uint8_t *fl = out_dev ? flags + lo : (uint8_t *)outbuf.ptr;
         if ((st = resolve_and_insert(h, A, fl, s)) != LSHB_OK) return st;
         BCK(cudaEventRecord(h->ev_t[2], s));

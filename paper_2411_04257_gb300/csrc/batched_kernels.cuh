@@ -1,7 +1,7 @@
 // Device side of the batched form: the per-chunk parameter block, the item
 // bookkeeping kernels (counts, scan, item -> document map) and the persistent
 // fused kernel k_batched (SHA-1 + MinHash over a work queue of (document,
-// shingle range) items, band keys and the pre-batch probes of each document).
+// shingle range) items, then the band keys of each document).
 #pragma once
 
 #include "bloom_kernels.cuh"
@@ -23,9 +23,7 @@ struct DynParams {
 
 struct BatchArgs {
     DynParams *dyn;
-    uint32_t item_shingles, ngram, P, npc, bands, rows, k, sketch_log2, layout, band_key;
-    uint64_t m_bits, words_per_filter;
-    const uint32_t *filters;
+    uint32_t item_shingles, ngram, P, npc, bands, rows, band_key;
     uint32_t *item_count;      // D
     uint64_t *item_start;      // D+1
     uint64_t *block_sums;      // scan partials
@@ -34,9 +32,9 @@ struct BatchArgs {
     uint32_t *pending;         // D: items of the document not finished yet
     uint32_t *sig_partial;     // D x P: merged minima of split documents
     unsigned long long *queue;
-    uint64_t *keys, *miss, *cand;
-    uint8_t *prehit;
-    uint32_t *sketch1, *sketch2;
+    uint64_t *keys;            // D x bands
+    uint64_t *cand;            // D: cleared for the Bloom stage
+    uint8_t *prehit;           // D: cleared for the Bloom stage
     uint32_t *error;
     PermSlice c;
 };
@@ -191,19 +189,13 @@ __global__ void __launch_bounds__(kBatchThreads) k_batched(const __grid_constant
             for (int t = 0; t < PPL; ++t)
                 if (lane + 32 * t < (int)A.npc) mn[t] = __ldcg(row + lane + 32 * t);
         }
-        // band keys (Sec. 4.1) and the probes of this document (Sec. 4.2)
+        // band keys of this document (Sec. 4.1)
         __syncwarp();
 #pragma unroll
         for (int t = 0; t < PPL; ++t) sigbuf[lane + 32 * t] = mn[t];
         __syncwarp();
-        for (uint32_t j = lane; j < A.bands; j += 32) {
-            const uint64_t key = band_key_of(sigbuf + j * A.rows, A.rows, j, A.band_key);
-            A.keys[d * A.bands + j] = key;
-            A.miss[d * A.bands + j] =
-                probe_band(A.filters + (uint64_t)j * A.words_per_filter, A.words_per_filter, key, j, A.k,
-                           A.m_bits, A.layout,
-                           A.sketch1, A.sketch2, A.sketch_log2);
-        }
+        for (uint32_t j = lane; j < A.bands; j += 32)
+            A.keys[d * A.bands + j] = band_key_of(sigbuf + j * A.rows, A.rows, j, A.band_key);
         __syncwarp();
     }
 }

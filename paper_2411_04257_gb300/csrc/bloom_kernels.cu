@@ -6,71 +6,57 @@
 // The batch is judged in parallel.  A band of document d hits when each of its
 // k probed bits is set before the batch or by an inserted document d' < d of
 // the batch.  The kernels below find that without a sort:
-//   1. probe_mark   reads the pre-batch bits; records, per (doc, band), which
-//                   probes found a clear bit ("missing"); marks each missing
-//                   bit in a two-level sketch (seen once / seen twice);
-//   2. classify     a band whose every missing bit was marked twice is a
-//                   candidate (some other document may set those bits); a
-//                   document with a band with no missing bit is a duplicate
-//                   whatever the order; one with neither is not a duplicate;
-//                   the rest are "uncertain";
-//   3. resolve      uncertain documents only: their candidate bits go into a
-//                   hash table; every inserting document records itself as a
-//                   setter with atomicMin; uncertain documents iterate
-//                   ins <- not dup(ins) (a Jacobi sweep) until nothing changes,
-//                   which is the unique sequential answer because document d
-//                   depends only on documents before it;
-//   4. insert       atomicOr of the missing bits of inserted documents.
+//   1. probe     reads the pre-batch bits; records, per (band, doc), which
+//                probes found a clear bit ("missing"); marks each missing bit
+//                in the band's sketch of 2-bit cells (seen once / twice);
+//   2. classify  a band whose every missing bit was marked twice is a
+//                candidate (some other document may set those bits); a
+//                document with a band with no missing bit is a duplicate
+//                whatever the order; one with neither is not a duplicate;
+//                the rest are "uncertain";
+//   3. resolve   uncertain documents only: their candidate bits go into a
+//                hash table with one segment per band; every inserting
+//                document records itself as a setter with atomicMin;
+//                uncertain documents iterate ins <- not dup(ins) (a Jacobi
+//                sweep) until nothing changes.  Document d depends only on
+//                documents before it, so the fixed point is unique and is
+//                the sequential answer; after t sweeps the first t uncertain
+//                documents are final, and an in-order pass (one warp) can
+//                finish from there;
+//   4. insert    atomicOr of the missing bits of inserted documents.
 // Sketch collisions only add candidates; they never drop one, so the result
-// is exact.
+// is exact.  Every (band, document) kernel runs band by band (a 2-D grid with
+// the band as its slow index): the filter and sketch of one band stay in L2
+// while its documents are processed.
 #include "bloom_kernels.cuh"
 
 namespace lshb {
 
-__global__ void k_probe_mark(const __grid_constant__ BloomArgs A) {
-    const uint64_t n = A.D * A.bands;
-    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
-         idx += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t j = (uint32_t)(idx % A.bands);
-        const uint32_t *F = A.filters + (uint64_t)j * A.words_per_filter;
-        if (A.k <= 24 && A.layout != 2) {
-            const ProbeSeq ps(A.keys[idx], j, A.m_bits, A.layout);
-            A.miss[idx] = probe_band_unrolled<24>(F, ps, j, A.k, A.m_bits, A.sketch1, A.sketch2,
-                                                  A.sketch_bits_log2);
-        } else {
-            A.miss[idx] = probe_band(F, A.words_per_filter, A.keys[idx], j, A.k, A.m_bits, A.layout,
-                                     A.sketch1, A.sketch2, A.sketch_bits_log2);
-        }
-    }
+// ---- probe and classification ----------------------------------------------------
+
+__global__ void __launch_bounds__(kBloomThreads) k_probe(const __grid_constant__ BloomArgs A) {
+    const uint64_t d = (uint64_t)blockIdx.x * kBloomThreads + threadIdx.x;
+    const uint32_t j = blockIdx.y;
+    if (d >= batch_docs(A)) return;
+    const uint64_t miss = probe_key<24>(A, j, A.keys[d * A.bands + j]);
+    A.miss[(uint64_t)j * A.mstride + d] = miss;
+    if (!miss) A.prehit[d] = 1;
 }
 
-__device__ __forceinline__ uint64_t batch_docs(const BloomArgs &A) {
-    return A.D_dev ? *A.D_dev : A.D;
-}
-
-__global__ void k_classify(const __grid_constant__ BloomArgs A) {
-    const uint64_t n = batch_docs(A) * A.bands;
-    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
-         idx += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t d = idx / A.bands;
-        const uint32_t j = (uint32_t)(idx % A.bands);
-        const uint64_t miss = A.miss[idx];
-        if (miss == 0) {
-            A.prehit[d] = 1;
-            continue;
-        }
-        const ProbeSeq ps(A.keys[idx], j, A.m_bits, A.layout);
-        bool all = true;
-        uint64_t mm = miss;
-        while (mm && all) {
-            const uint32_t u = __ffsll((long long)mm) - 1;
-            mm &= mm - 1;
-            const uint64_t g = (uint64_t)j * A.m_bits + ps.pos(u);
-            const uint64_t si = sketch_index(g, A.sketch_bits_log2);
-            all = (__ldg(A.sketch2 + (si >> 5)) >> (si & 31)) & 1u;
-        }
-        if (all) atomicOr((unsigned long long *)(A.cand + d), 1ull << j);
+__global__ void __launch_bounds__(kBloomThreads) k_classify(const __grid_constant__ BloomArgs A) {
+    const uint64_t d = (uint64_t)blockIdx.x * kBloomThreads + threadIdx.x;
+    const uint32_t j = blockIdx.y;
+    if (d >= batch_docs(A)) return;
+    uint64_t mm = A.miss[(uint64_t)j * A.mstride + d];
+    if (!mm) return;
+    const ProbeSeq ps(A.keys[d * A.bands + j], j, A.m_bits, A.layout);
+    bool all = true;
+    while (mm && all) {
+        const uint32_t u = __ffsll((long long)mm) - 1;
+        mm &= mm - 1;
+        all = sketch_twice(A, j, ps.pos(u));
     }
+    if (all) atomicOr((unsigned long long *)(A.cand + d), 1ull << j);
 }
 
 // Status per document and the per-block count of uncertain documents.
@@ -95,7 +81,7 @@ __global__ void __launch_bounds__(1024) k_status(const __grid_constant__ BloomAr
 }
 
 // Exclusive scan of the block counts (one block; nb up to a few thousand) and
-// the total in counters[0].
+// the total in *total.
 __global__ void __launch_bounds__(1024) k_scan_counts(uint32_t *block_counts, uint32_t nb,
                                                       uint32_t *total) {
     __shared__ uint32_t part[1024];
@@ -146,125 +132,150 @@ __global__ void __launch_bounds__(1024) k_compact(const __grid_constant__ BloomA
 
 // ---- exact resolution of uncertain documents --------------------------------
 
-constexpr uint64_t kEmpty = ~0ull;
-constexpr uint32_t kNone = 0xffffffffu;
-
-__device__ __forceinline__ uint32_t ht_find(const uint64_t *keys, uint32_t mask, uint64_t g) {
-    uint32_t s = (uint32_t)(mix64(g) & mask);
+__device__ __forceinline__ uint32_t ht_find(const ResolveTable &T, uint32_t j, uint64_t pos) {
+    const uint64_t base = T.seg_base[j];
+    const uint32_t mask = T.seg_mask[j];
+    if (pos == ~0ull) {
+        const uint64_t s = base + mask + 1;
+        return T.keys[s] == 0ull ? (uint32_t)s : kNone;
+    }
+    uint32_t s = (uint32_t)(mix64(pos) & mask);
     for (uint32_t i = 0; i <= mask; ++i) {
-        const uint64_t k = keys[s];
-        if (k == g) return s;
-        if (k == kEmpty) return kNone;
+        const uint64_t k = T.keys[base + s];
+        if (k == pos) return (uint32_t)(base + s);
+        if (k == ~0ull) return kNone;
         s = (s + 1) & mask;
     }
     return kNone;
 }
 
-__device__ __forceinline__ bool ht_insert(uint64_t *keys, uint32_t mask, uint64_t g) {
-    uint32_t s = (uint32_t)(mix64(g) & mask);
+__device__ __forceinline__ bool ht_insert(const ResolveTable &T, uint32_t j, uint64_t pos) {
+    const uint64_t base = T.seg_base[j];
+    const uint32_t mask = T.seg_mask[j];
+    if (pos == ~0ull) {
+        T.keys[base + mask + 1] = 0ull;
+        return true;
+    }
+    uint32_t s = (uint32_t)(mix64(pos) & mask);
     for (uint32_t i = 0; i <= mask; ++i) {
-        const unsigned long long prev =
-            atomicCAS((unsigned long long *)(keys + s), (unsigned long long)kEmpty,
-                      (unsigned long long)g);
-        if (prev == kEmpty || prev == g) return true;
+        const unsigned long long prev = atomicCAS((unsigned long long *)(T.keys + base + s),
+                                                  ~0ull, (unsigned long long)pos);
+        if (prev == ~0ull || prev == pos) return true;
         s = (s + 1) & mask;
     }
     return false;
 }
 
-// Number of candidate bits of the uncertain documents (sizes the table).
-__global__ void k_count_keys(const __grid_constant__ BloomArgs A, const uint32_t *ulist,
-                             uint32_t nu, unsigned long long *count) {
-    const uint64_t n = (uint64_t)nu * A.bands;
-    unsigned long long local = 0;
-    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
-         idx += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t d = ulist[idx / A.bands];
-        const uint32_t j = (uint32_t)(idx % A.bands);
-        if ((A.cand[d] >> j) & 1ull) local += __popcll(A.miss[d * A.bands + j]);
+// Candidate bits of the uncertain documents, per band (sizes the segments).
+__global__ void __launch_bounds__(kBloomThreads) k_count_keys(const __grid_constant__ BloomArgs A,
+                                                              const uint32_t *ulist, uint32_t nu,
+                                                              unsigned long long *band_counts) {
+    __shared__ unsigned long long part[kBloomThreads / 32];
+    const uint32_t ui = blockIdx.x * kBloomThreads + threadIdx.x;
+    const uint32_t j = blockIdx.y;
+    unsigned long long c = 0;
+    if (ui < nu) {
+        const uint32_t d = ulist[ui];
+        if ((A.cand[d] >> j) & 1ull) c = __popcll(A.miss[(uint64_t)j * A.mstride + d]);
     }
-    if (local) atomicAdd(count, local);
+    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(LSHB_FULL_MASK, c, off);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long s = 0;
+        for (int w = 0; w < kBloomThreads / 32; ++w) s += part[w];
+        if (s) atomicAdd(band_counts + j, s);
+    }
 }
 
-__global__ void k_rk_insert(const __grid_constant__ BloomArgs A, const uint32_t *ulist, uint32_t nu,
-                            ResolveTable T) {
-    const uint64_t n = (uint64_t)nu * A.bands;
-    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
-         idx += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t d = ulist[idx / A.bands];
-        const uint32_t j = (uint32_t)(idx % A.bands);
-        if (!((A.cand[d] >> j) & 1ull)) continue;
-        const ProbeSeq ps(A.keys[d * A.bands + j], j, A.m_bits, A.layout);
-        uint64_t mm = A.miss[d * A.bands + j];
-        while (mm) {
-            const uint32_t u = __ffsll((long long)mm) - 1;
-            mm &= mm - 1;
-            const uint64_t g = (uint64_t)j * A.m_bits + ps.pos(u);
-            if (!ht_insert(T.keys, T.mask, g)) atomicOr(A.error, kErrTableFull);
-        }
+__global__ void __launch_bounds__(kBloomThreads) k_rk_insert(const __grid_constant__ BloomArgs A,
+                                                             const uint32_t *ulist, uint32_t nu,
+                                                             const __grid_constant__ ResolveTable T) {
+    const uint32_t ui = blockIdx.x * kBloomThreads + threadIdx.x;
+    const uint32_t j = blockIdx.y;
+    if (ui >= nu) return;
+    const uint32_t d = ulist[ui];
+    if (!((A.cand[d] >> j) & 1ull)) return;
+    const ProbeSeq ps(A.keys[(uint64_t)d * A.bands + j], j, A.m_bits, A.layout);
+    uint64_t mm = A.miss[(uint64_t)j * A.mstride + d];
+    while (mm) {
+        const uint32_t u = __ffsll((long long)mm) - 1;
+        mm &= mm - 1;
+        if (!ht_insert(T, j, ps.pos(u))) atomicOr(A.error, kErrTableFull);
     }
 }
 
 // Fixed setters: documents whose insertion does not depend on the order.
 // NONDUP mode: status 0; INSERT_ALL mode: every document.
-__global__ void k_fixed_setters(const __grid_constant__ BloomArgs A, ResolveTable T,
-                                int insert_all) {
-    const uint64_t n = A.D * A.bands;
-    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
-         idx += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t d = idx / A.bands;
-        if (!insert_all && A.status[d] != 0) continue;
-        const uint32_t j = (uint32_t)(idx % A.bands);
-        uint64_t mm = A.miss[idx];
-        if (!mm) continue;
-        const ProbeSeq ps(A.keys[idx], j, A.m_bits, A.layout);
-        while (mm) {
-            const uint32_t u = __ffsll((long long)mm) - 1;
-            mm &= mm - 1;
-            const uint64_t g = (uint64_t)j * A.m_bits + ps.pos(u);
-            const uint32_t s = ht_find(T.keys, T.mask, g);
-            if (s != kNone) atomicMin(T.first_fixed + s, (uint32_t)d);
-        }
+__global__ void __launch_bounds__(kBloomThreads) k_fixed_setters(
+    const __grid_constant__ BloomArgs A, const __grid_constant__ ResolveTable T, int insert_all) {
+    const uint64_t d = (uint64_t)blockIdx.x * kBloomThreads + threadIdx.x;
+    const uint32_t j = blockIdx.y;
+    if (d >= A.D) return;
+    if (!insert_all && A.status[d] != 0) return;
+    uint64_t mm = A.miss[(uint64_t)j * A.mstride + d];
+    if (!mm) return;
+    const ProbeSeq ps(A.keys[d * A.bands + j], j, A.m_bits, A.layout);
+    while (mm) {
+        const uint32_t u = __ffsll((long long)mm) - 1;
+        mm &= mm - 1;
+        const uint32_t s = ht_find(T, j, ps.pos(u));
+        if (s != kNone) atomicMin(T.first_fixed + s, (uint32_t)d);
     }
 }
 
 // Table slot of every missing bit of every uncertain document (all bands).
-__global__ void k_cache_slots(const __grid_constant__ BloomArgs A, const uint32_t *ulist,
-                              uint32_t nu, ResolveTable T) {
-    const uint64_t n = (uint64_t)nu * A.bands;
-    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
-         idx += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t d = ulist[idx / A.bands];
-        const uint32_t j = (uint32_t)(idx % A.bands);
-        const uint64_t miss = A.miss[d * A.bands + j];
-        const ProbeSeq ps(A.keys[d * A.bands + j], j, A.m_bits, A.layout);
-        uint32_t *out = T.slots + idx * A.k;
-        for (uint32_t u = 0; u < A.k; ++u) {
-            uint32_t s = kNone;
-            if ((miss >> u) & 1ull) s = ht_find(T.keys, T.mask, (uint64_t)j * A.m_bits + ps.pos(u));
-            out[u] = s;
-        }
-    }
+__global__ void __launch_bounds__(kBloomThreads) k_cache_slots(const __grid_constant__ BloomArgs A,
+                                                               const uint32_t *ulist, uint32_t nu,
+                                                               const __grid_constant__ ResolveTable T) {
+    const uint32_t ui = blockIdx.x * kBloomThreads + threadIdx.x;
+    const uint32_t j = blockIdx.y;
+    if (ui >= nu) return;
+    const uint32_t d = ulist[ui];
+    const uint64_t miss = A.miss[(uint64_t)j * A.mstride + d];
+    const ProbeSeq ps(A.keys[(uint64_t)d * A.bands + j], j, A.m_bits, A.layout);
+    uint32_t *out = T.slots + ((uint64_t)ui * A.bands + j) * A.k;
+    for (uint32_t u = 0; u < A.k; ++u)
+        out[u] = ((miss >> u) & 1ull) ? ht_find(T, j, ps.pos(u)) : kNone;
 }
 
-__global__ void k_iter_reset(ResolveTable T) {
-    for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s <= T.mask;
+// Sweep control.  A sweep runs only while the previous one changed an insert
+// decision; the host enqueues sweeps in groups and reads ctl once per group.
+__device__ __forceinline__ bool sweeps_done(const ResolveTable &T) {
+    return __ldcg(T.ctl + 1) != 0u;
+}
+
+__global__ void k_sweep_begin(const __grid_constant__ ResolveTable T) {
+    if (T.ctl[1]) return;
+    if (T.ctl[2] > 0 && T.ctl[0] == 0) {
+        T.ctl[1] = 1u;
+        return;
+    }
+    T.ctl[0] = 0u;
+    T.ctl[2] += 1u;
+}
+
+__global__ void k_iter_reset(const __grid_constant__ ResolveTable T, uint64_t table_slots,
+                             int forced) {
+    if (!forced && sweeps_done(T)) return;
+    for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < table_slots;
          s += (uint64_t)gridDim.x * blockDim.x)
         T.first[s] = T.first_fixed[s];
 }
 
-__global__ void k_iter_setters(const __grid_constant__ BloomArgs A, const uint32_t *ulist,
-                               uint32_t nu, ResolveTable T) {
-    const uint64_t n = (uint64_t)nu * A.bands;
-    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
-         idx += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t ui = (uint32_t)(idx / A.bands);
-        if (!T.ins[ui]) continue;
-        const uint32_t d = ulist[ui];
-        const uint32_t *sl = T.slots + idx * A.k;
-        for (uint32_t u = 0; u < A.k; ++u)
-            if (sl[u] != kNone) atomicMin(T.first + sl[u], d);
-    }
+// Setters of the current sweep (uncertain documents ui < n_set with ins set),
+// one (document, band) per thread.
+__global__ void __launch_bounds__(kBloomThreads) k_iter_setters(const __grid_constant__ BloomArgs A,
+                                                                const uint32_t *ulist, uint32_t n_set,
+                                                                const __grid_constant__ ResolveTable T,
+                                                                int forced) {
+    if (!forced && sweeps_done(T)) return;
+    const uint32_t ui = blockIdx.x * kBloomThreads + threadIdx.x;
+    if (ui >= n_set || !T.ins[ui]) return;
+    const uint32_t d = ulist[ui];
+    const uint32_t *sl = T.slots + ((uint64_t)ui * A.bands + blockIdx.y) * A.k;
+    for (uint32_t u = 0; u < A.k; ++u)
+        if (sl[u] != kNone) atomicMin(T.first + sl[u], d);
 }
 
 __device__ __forceinline__ bool uncertain_is_dup(const BloomArgs &A, const ResolveTable &T,
@@ -284,7 +295,8 @@ __device__ __forceinline__ bool uncertain_is_dup(const BloomArgs &A, const Resol
 }
 
 __global__ void k_iter_eval(const __grid_constant__ BloomArgs A, const uint32_t *ulist, uint32_t nu,
-                            ResolveTable T, int insert_all) {
+                            const __grid_constant__ ResolveTable T, int insert_all) {
+    if (sweeps_done(T)) return;
     for (uint32_t ui = blockIdx.x * blockDim.x + threadIdx.x; ui < nu; ui += gridDim.x * blockDim.x) {
         const uint32_t d = ulist[ui];
         const bool dup = uncertain_is_dup(A, T, ui, d);
@@ -292,34 +304,54 @@ __global__ void k_iter_eval(const __grid_constant__ BloomArgs A, const uint32_t 
         const uint8_t ins = insert_all ? 1 : (dup ? 0 : 1);
         if (ins != T.ins[ui]) {
             T.ins[ui] = ins;
-            atomicOr(T.changed, 1u);
+            T.ctl[0] = 1u;
         }
     }
 }
 
-// In-order pass over the uncertain documents (one thread): the sequential
-// definition itself, used when the Jacobi sweep has not settled.
-__global__ void k_sequential(const __grid_constant__ BloomArgs A, const uint32_t *ulist, uint32_t nu,
-                             ResolveTable T) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    for (uint64_t s = 0; s <= T.mask; ++s) T.first[s] = T.first_fixed[s];
-    for (uint32_t ui = 0; ui < nu; ++ui) {
+// The sequential definition, resumed at uncertain document `settled` (the
+// earlier ones are final): one warp takes the remaining documents in order;
+// its lanes split each document's probed slots.  `first` holds the fixed
+// setters and the settled documents' insertions when it starts.
+__global__ void __launch_bounds__(32) k_in_order(const __grid_constant__ BloomArgs A,
+                                                 const uint32_t *ulist, uint32_t nu,
+                                                 const __grid_constant__ ResolveTable T,
+                                                 uint32_t settled) {
+    const uint32_t lane = threadIdx.x;
+    const uint32_t nslots = A.bands * A.k;
+    for (uint32_t ui = settled; ui < nu; ++ui) {
         const uint32_t d = ulist[ui];
-        const bool dup = uncertain_is_dup(A, T, ui, d);
-        T.udup[ui] = dup;
-        T.ins[ui] = dup ? 0 : 1;
-        if (!dup) {
-            const uint32_t *sl = T.slots + (uint64_t)ui * A.bands * A.k;
-            for (uint64_t t = 0; t < (uint64_t)A.bands * A.k; ++t)
-                if (sl[t] != kNone && T.first[sl[t]] > d) T.first[sl[t]] = d;
+        const uint64_t cand = A.cand[d];
+        const uint32_t *sl = T.slots + (uint64_t)ui * nslots;
+        bool dup = false;
+        for (uint32_t j = 0; j < A.bands && !dup; ++j) {
+            if (!((cand >> j) & 1ull)) continue;
+            bool all = true;
+            for (uint32_t u = lane; u < A.k; u += 32) {
+                const uint32_t s = sl[j * A.k + u];
+                if (s != kNone && __ldcg(T.first + s) >= d) all = false;
+            }
+            dup = __all_sync(LSHB_FULL_MASK, all);
         }
+        if (lane == 0) {
+            T.udup[ui] = dup;
+            T.ins[ui] = dup ? 0 : 1;
+        }
+        if (!dup) {
+            uint32_t sink = 0;
+            for (uint32_t t = lane; t < nslots; t += 32)
+                if (sl[t] != kNone) sink |= atomicMin(T.first + sl[t], d);
+            __threadfence();
+            if (sink == 0x7fffffffu) T.ctl[3] = sink;  // keeps the returning atomics
+        }
+        __syncwarp();
     }
 }
 
 // Flags and insert decisions of every document.
 __global__ void k_finalize(const __grid_constant__ BloomArgs A, const uint32_t *ulist, uint32_t nu,
-                           ResolveTable T, int insert_all, uint8_t *flags, uint8_t *insd,
-                           unsigned long long *dup_count) {
+                           const __grid_constant__ ResolveTable T, int insert_all, uint8_t *flags,
+                           uint8_t *insd, unsigned long long *dup_count) {
     for (uint64_t d = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; d < A.D;
          d += (uint64_t)gridDim.x * blockDim.x) {
         const uint8_t st = A.status[d];
@@ -339,28 +371,25 @@ __global__ void k_finalize(const __grid_constant__ BloomArgs A, const uint32_t *
     }
 }
 
-__global__ void k_insert(const __grid_constant__ BloomArgs A, const uint8_t *insd) {
-    const uint64_t n = A.D * A.bands;
-    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
-         idx += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t d = idx / A.bands;
-        if (!insd[d]) continue;
-        uint64_t mm = A.miss[idx];
-        if (!mm) continue;
-        const uint32_t j = (uint32_t)(idx % A.bands);
-        uint32_t *F = A.filters + (uint64_t)j * A.words_per_filter;
-        if (A.layout == 2) {
-            if (!exact_insert(reinterpret_cast<uint64_t *>(F), A.words_per_filter / 2, A.keys[idx]))
-                atomicOr(A.error, kErrTableFull);
-            continue;
-        }
-        const ProbeSeq ps(A.keys[idx], j, A.m_bits, A.layout);
-        while (mm) {
-            const uint32_t u = __ffsll((long long)mm) - 1;
-            mm &= mm - 1;
-            const uint64_t q = ps.pos(u);
-            atomicOr(F + (q >> 5), 1u << (q & 31));
-        }
+__global__ void __launch_bounds__(kBloomThreads) k_insert(const __grid_constant__ BloomArgs A,
+                                                          const uint8_t *insd) {
+    const uint64_t d = (uint64_t)blockIdx.x * kBloomThreads + threadIdx.x;
+    const uint32_t j = blockIdx.y;
+    if (d >= A.D || !insd[d]) return;
+    uint64_t mm = A.miss[(uint64_t)j * A.mstride + d];
+    if (!mm) return;
+    uint32_t *F = A.filters + (uint64_t)j * A.words_per_filter;
+    if (A.layout == 2) {
+        if (!exact_insert(reinterpret_cast<uint64_t *>(F), A.exact_cap, A.keys[d * A.bands + j]))
+            atomicOr(A.error, kErrTableFull);
+        return;
+    }
+    const ProbeSeq ps(A.keys[d * A.bands + j], j, A.m_bits, A.layout);
+    while (mm) {
+        const uint32_t u = __ffsll((long long)mm) - 1;
+        mm &= mm - 1;
+        const uint64_t q = ps.pos(u);
+        atomicOr(F + (q >> 5), 1u << (q & 31));
     }
 }
 
@@ -369,6 +398,16 @@ __global__ void k_popcount(const uint32_t *__restrict__ w, uint64_t n, unsigned 
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x)
         c += __popc(w[i]);
+    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(LSHB_FULL_MASK, c, off);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+__global__ void k_count_occupied(const uint64_t *__restrict__ slots, uint64_t n,
+                                 unsigned long long *out) {
+    unsigned long long c = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        c += slots[i] != ~0ull;
     for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(LSHB_FULL_MASK, c, off);
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
@@ -388,20 +427,16 @@ static int grid_for(uint64_t n, int threads) {
     return (int)(want == 0 ? 1 : (want < cap ? want : cap));
 }
 
+// (document blocks, bands) grid for n documents.
+static dim3 band_grid(uint64_t n, uint32_t bands) {
+    const uint64_t bx = (n + kBloomThreads - 1) / kBloomThreads;
+    return dim3((unsigned)(bx ? bx : 1), bands, 1);
+}
+
 cudaError_t launch_popcount(const uint32_t *words, uint64_t n, unsigned long long *out,
                             cudaStream_t s) {
     k_popcount<<<grid_for(n, 256), 256, 0, s>>>(words, n, out); count_launch();
     return cudaGetLastError();
-}
-
-__global__ void k_count_occupied(const uint64_t *__restrict__ slots, uint64_t n,
-                                 unsigned long long *out) {
-    unsigned long long c = 0;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x)
-        c += slots[i] != ~0ull;
-    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(LSHB_FULL_MASK, c, off);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
 
 cudaError_t launch_count_occupied(const uint64_t *slots, uint64_t n, unsigned long long *out,
@@ -410,46 +445,59 @@ cudaError_t launch_count_occupied(const uint64_t *slots, uint64_t n, unsigned lo
     return cudaGetLastError();
 }
 
-cudaError_t launch_probe_mark(const BloomArgs &a, cudaStream_t s) {
-    k_probe_mark<<<grid_for(a.D * a.bands, 256), 256, 0, s>>>(a); count_launch();
+cudaError_t launch_probe(const BloomArgs &a, uint64_t dcap, cudaStream_t s) {
+    k_probe<<<band_grid(dcap, a.bands), kBloomThreads, 0, s>>>(a); count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_classify(const BloomArgs &a, uint32_t *block_counts, uint32_t *total,
-                            uint32_t *ulist, cudaStream_t s) {
-    k_classify<<<grid_for(a.D * a.bands, 256), 256, 0, s>>>(a); count_launch();
-    const uint32_t nb = (uint32_t)((a.D + 1023) / 1024);
-    k_status<<<nb, 1024, 0, s>>>(a, block_counts); count_launch();
-    k_scan_counts<<<1, 1024, 0, s>>>(block_counts, nb, total); count_launch();
-    k_compact<<<nb, 1024, 0, s>>>(a, block_counts, ulist); count_launch();
+cudaError_t launch_classify(const BloomArgs &a, uint64_t dcap, uint32_t *block_counts,
+                            uint32_t *total, uint32_t *ulist, cudaStream_t s) {
+    k_classify<<<band_grid(dcap, a.bands), kBloomThreads, 0, s>>>(a); count_launch();
+    const uint32_t nb = (uint32_t)((dcap + 1023) / 1024);
+    k_status<<<nb ? nb : 1, 1024, 0, s>>>(a, block_counts); count_launch();
+    k_scan_counts<<<1, 1024, 0, s>>>(block_counts, nb ? nb : 1, total); count_launch();
+    k_compact<<<nb ? nb : 1, 1024, 0, s>>>(a, block_counts, ulist); count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_count_keys(const BloomArgs &a, const uint32_t *ulist, uint32_t nu,
-                              unsigned long long *count, cudaStream_t s) {
-    k_count_keys<<<grid_for((uint64_t)nu * a.bands, 256), 256, 0, s>>>(a, ulist, nu, count); count_launch();
+                              unsigned long long *band_counts, cudaStream_t s) {
+    k_count_keys<<<band_grid(nu, a.bands), kBloomThreads, 0, s>>>(a, ulist, nu, band_counts);
+    count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_resolve_setup(const BloomArgs &a, const uint32_t *ulist, uint32_t nu,
                                  const ResolveTable &t, int insert_all, cudaStream_t s) {
-    k_rk_insert<<<grid_for((uint64_t)nu * a.bands, 256), 256, 0, s>>>(a, ulist, nu, t); count_launch();
-    k_fixed_setters<<<grid_for(a.D * a.bands, 256), 256, 0, s>>>(a, t, insert_all); count_launch();
-    k_cache_slots<<<grid_for((uint64_t)nu * a.bands, 128), 128, 0, s>>>(a, ulist, nu, t); count_launch();
+    k_rk_insert<<<band_grid(nu, a.bands), kBloomThreads, 0, s>>>(a, ulist, nu, t); count_launch();
+    k_fixed_setters<<<band_grid(a.D, a.bands), kBloomThreads, 0, s>>>(a, t, insert_all);
+    count_launch();
+    k_cache_slots<<<band_grid(nu, a.bands), kBloomThreads, 0, s>>>(a, ulist, nu, t); count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_resolve_iteration(const BloomArgs &a, const uint32_t *ulist, uint32_t nu,
-                                     const ResolveTable &t, int insert_all, cudaStream_t s) {
-    k_iter_reset<<<grid_for((uint64_t)t.mask + 1, 256), 256, 0, s>>>(t); count_launch();
-    if (!insert_all) k_iter_setters<<<grid_for((uint64_t)nu * a.bands, 256), 256, 0, s>>>(a, ulist, nu, t); count_launch();
+cudaError_t launch_resolve_sweep(const BloomArgs &a, const uint32_t *ulist, uint32_t nu,
+                                 const ResolveTable &t, uint64_t table_slots, int insert_all,
+                                 cudaStream_t s) {
+    k_sweep_begin<<<1, 1, 0, s>>>(t); count_launch();
+    k_iter_reset<<<grid_for(table_slots, 256), 256, 0, s>>>(t, table_slots, 0); count_launch();
+    if (!insert_all) {
+        k_iter_setters<<<band_grid(nu, a.bands), kBloomThreads, 0, s>>>(a, ulist, nu, t, 0);
+        count_launch();
+    }
     k_iter_eval<<<grid_for(nu, 256), 256, 0, s>>>(a, ulist, nu, t, insert_all); count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_resolve_sequential(const BloomArgs &a, const uint32_t *ulist, uint32_t nu,
-                                      const ResolveTable &t, cudaStream_t s) {
-    k_sequential<<<1, 1, 0, s>>>(a, ulist, nu, t); count_launch();
+cudaError_t launch_resolve_in_order(const BloomArgs &a, const uint32_t *ulist, uint32_t nu,
+                                    const ResolveTable &t, uint64_t table_slots,
+                                    uint32_t settled, cudaStream_t s) {
+    k_iter_reset<<<grid_for(table_slots, 256), 256, 0, s>>>(t, table_slots, 1); count_launch();
+    if (settled > 0) {
+        k_iter_setters<<<band_grid(settled, a.bands), kBloomThreads, 0, s>>>(a, ulist, settled, t, 1);
+        count_launch();
+    }
+    k_in_order<<<1, 32, 0, s>>>(a, ulist, nu, t, settled); count_launch();
     return cudaGetLastError();
 }
 
@@ -458,7 +506,7 @@ cudaError_t launch_finalize_insert(const BloomArgs &a, const uint32_t *ulist, ui
                                    uint8_t *insd, unsigned long long *dup_count, cudaStream_t s) {
     k_finalize<<<grid_for(a.D, 256), 256, 0, s>>>(a, ulist, nu, t, insert_all, flags, insd,
                                                    dup_count); count_launch();
-    k_insert<<<grid_for(a.D * a.bands, 256), 256, 0, s>>>(a, insd); count_launch();
+    k_insert<<<band_grid(a.D, a.bands), kBloomThreads, 0, s>>>(a, insd); count_launch();
     return cudaGetLastError();
 }
 

@@ -310,12 +310,15 @@ lshb_status lshb::init_handle(lshbloom *h, const lshb_config *cfg) {
     h->words_per_filter = ((h->m / 32) + 31) / 32 * 32;  // 128-byte aligned filters
     if (h->layout == LSHB_EXACT_KEYS) {
         // One table of uint64 keys per band, at most half full at n_expected;
-        // the key itself is the one "position" (global id band * 2^58 + key).
+        // the key itself is the one "position".  Slot `cap` records the key
+        // 2^64 - 1 (the empty marker of the others); the table is padded to
+        // a multiple of 128 bytes like the filters.
         uint64_t cap = 1024;
         while (cap < 2 * cfg->n_expected) cap <<= 1;
         h->k = 1;
         h->m = 1ull << 58;
-        h->words_per_filter = cap * 2;
+        h->exact_cap = cap;
+        h->words_per_filter = ((cap + 1) * 2 + 31) / 32 * 32;
     }
     h->a.resize(h->P);
     h->b.resize(h->P);
@@ -357,9 +360,9 @@ lshb_status lshb::init_handle(lshbloom *h, const lshb_config *cfg) {
         return fail(LSHB_ERR_OOM, "filters: %zu bytes", fbytes);
     }
     CK(cudaMemsetAsync(h->filters, h->layout == LSHB_EXACT_KEYS ? 0xff : 0, fbytes, h->stream));
-    CK(cudaMalloc(&h->counters, 256));
-    CK(cudaMemsetAsync(h->counters, 0, 256, h->stream));
-    CK(cudaMallocHost(&h->host_counters, 256));
+    CK(cudaMalloc(&h->counters, kCounterBytes));
+    CK(cudaMemsetAsync(h->counters, 0, kCounterBytes, h->stream));
+    CK(cudaMallocHost(&h->host_counters, kCounterBytes));
     CK(cudaStreamSynchronize(h->stream));
     return LSHB_OK;
 }
@@ -525,14 +528,9 @@ lshb_status lshb::ensure_chunk_scratch(lshbloom *h, uint64_t Dc, uint64_t Tc, bo
         if ((st = h->buf(B_SIG).reserve(Dc * h->P * 4)) != LSHB_OK) return st;
     if (plain_hashes)
         if ((st = h->buf(B_HASHES).reserve(std::max<uint64_t>(Tc, 1) * 4)) != LSHB_OK) return st;
-    // sketch: >= 8 bits per possible mark, at least 2^16 bits
-    uint64_t marks = std::max<uint64_t>(Dc * b * h->k * 8, 1ull << 16);
-    uint32_t lg = 16;
-    while ((1ull << lg) < marks && lg < 36) ++lg;
-    if (lg > h->sketch_log2_cap) h->sketch_log2_cap = lg;
-    const uint64_t sbytes = (1ull << h->sketch_log2_cap) / 8;
-    if ((st = h->buf(B_SKETCH1).reserve(sbytes)) != LSHB_OK) return st;
-    if ((st = h->buf(B_SKETCH2).reserve(sbytes)) != LSHB_OK) return st;
+    // sketch: one region of 2-bit cells per band
+    const uint64_t sbytes = (uint64_t)h->bands * (sketch_cells_for(h, Dc) / 16) * 4;
+    if ((st = h->buf(B_SKETCH).reserve(sbytes)) != LSHB_OK) return st;
     return LSHB_OK;
 }
 
@@ -622,7 +620,20 @@ lshb_status lshb::run_signatures(lshbloom *h, const ChunkIn &in, uint32_t *sig_o
     return LSHB_OK;
 }
 
-BloomArgs lshb::bloom_args(lshbloom *h, uint64_t D) {
+// Two cells per possible mark (b k per document and band): a missing bit of
+// one document is then marked by another unrelated one with probability
+// 1 - e^(-1/2), and all k = 17 missing bits of a band (a false candidate)
+// with probability about 1e-7.
+uint64_t lshb::sketch_cells_for(const lshbloom *h, uint64_t dcap) {
+    const uint64_t cells = std::max<uint64_t>(2 * std::max<uint64_t>(dcap, 1) * h->k, 1024);
+    return (cells + 15) / 16 * 16;
+}
+
+uint64_t lshb::probe_sectors_per_key(const lshbloom *h) {
+    return h->layout == LSHB_BLOOM_STANDARD ? h->k : 1u;
+}
+
+BloomArgs lshb::bloom_args(lshbloom *h, uint64_t D, uint64_t dcap) {
     BloomArgs b;
     memset(&b, 0, sizeof b);
     b.D = D;
@@ -631,42 +642,35 @@ BloomArgs lshb::bloom_args(lshbloom *h, uint64_t D) {
     b.layout = h->layout;
     b.m_bits = h->m;
     b.words_per_filter = h->words_per_filter;
+    b.exact_cap = h->exact_cap;
     b.filters = h->filters;
     b.keys = (const uint64_t *)h->buf(B_KEYS).ptr;
     b.miss = (uint64_t *)h->buf(B_MISS).ptr;
-    b.sketch1 = (uint32_t *)h->buf(B_SKETCH1).ptr;
-    b.sketch2 = (uint32_t *)h->buf(B_SKETCH2).ptr;
+    b.mstride = dcap;
+    b.sketch = (uint32_t *)h->buf(B_SKETCH).ptr;
+    b.sketch_cells = sketch_cells_for(h, dcap);
     b.status = (uint8_t *)h->buf(B_STATUS).ptr;
     b.cand = (uint64_t *)h->buf(B_CAND).ptr;
     b.prehit = (uint8_t *)h->buf(B_PREHIT).ptr;
     b.error = h->counters + C_ERROR;
-    uint64_t marks = std::max<uint64_t>(D * h->bands * h->k * 8, 1ull << 16);
-    uint32_t lg = 16;
-    while ((1ull << lg) < marks && lg < h->sketch_log2_cap) ++lg;
-    b.sketch_bits_log2 = lg;
     return b;
 }
 
 // Bloom stage: probe, classify, resolve the uncertain documents, insert.
-// Writes flags into `flags_dev` (device, D bytes).
+// Band keys are in B_KEYS; writes flags into `flags_dev` (device, D bytes).
 lshb_status lshb::run_bloom(lshbloom *h, uint64_t D, uint8_t *flags_dev, cudaStream_t s) {
-    BloomArgs A = bloom_args(h, D);
-    const uint64_t sbytes = (1ull << A.sketch_bits_log2) / 8;
-    CK(cudaMemsetAsync(A.sketch1, 0, sbytes, s));
-    CK(cudaMemsetAsync(A.sketch2, 0, sbytes, s));
+    BloomArgs A = bloom_args(h, D, D);
+    CK(cudaMemsetAsync(A.sketch, 0, (uint64_t)h->bands * (A.sketch_cells / 16) * 4, s));
     CK(cudaMemsetAsync(A.cand, 0, D * 8, s));
     CK(cudaMemsetAsync(A.prehit, 0, D, s));
-    CK(cudaMemsetAsync(h->counters, 0, 64, s));
+    CK(cudaMemsetAsync(h->counters, 0, kChunkCounterBytes, s));
     CK(cudaEventRecord(h->ev_p[0], s));
-    CK(launch_probe_mark(A, s));
+    CK(launch_probe(A, D, s));
     CK(cudaEventRecord(h->ev_p[1], s));
-    h->probe_pending = true;
-    // distinct 32-byte sectors the probes address: k per band key, or one
-    // (the key's block) in the blocked layout
-    h->probe_sectors += D * h->bands * (h->layout == LSHB_BLOOM_STANDARD ? h->k : 1u);
+    h->probe_sectors += D * h->bands * probe_sectors_per_key(h);
     uint32_t *ulist = (uint32_t *)h->buf(B_ULIST).ptr;
-    CK(launch_classify(A, (uint32_t *)h->buf(B_BLOCKCNT).ptr, h->counters + C_NU, ulist, s));
-    CK(cudaMemcpyAsync(h->host_counters, h->counters, 64, cudaMemcpyDeviceToHost, s));
+    CK(launch_classify(A, D, (uint32_t *)h->buf(B_BLOCKCNT).ptr, h->counters + C_NU, ulist, s));
+    CK(cudaMemcpyAsync(h->host_counters, h->counters, kChunkCounterBytes, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     float ms_probe = 0.f;
     CK(cudaEventElapsedTime(&ms_probe, h->ev_p[0], h->ev_p[1]));
@@ -685,56 +689,72 @@ lshb_status lshb::resolve_and_insert(lshbloom *h, const BloomArgs &A, uint8_t *f
     memset(&T, 0, sizeof T);
     if (nu > 0) {
         h->uncertain_docs += nu;
-        unsigned long long *cnt = (unsigned long long *)(h->counters + C_KEYCOUNT);
-        CK(launch_count_keys(A, ulist, nu, cnt, s));
-        CK(cudaMemcpyAsync(h->host_counters, h->counters, 64, cudaMemcpyDeviceToHost, s));
+        // candidate bits per band size the table's segments
+        unsigned long long *bc = (unsigned long long *)(h->counters + C_BANDCOUNT);
+        CK(cudaMemsetAsync(bc, 0, 8 * kMaxBands, s));
+        CK(launch_count_keys(A, ulist, nu, bc, s));
+        CK(cudaMemcpyAsync(h->host_counters + C_BANDCOUNT, bc, 8 * kMaxBands,
+                           cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        const uint64_t nkeys = *(unsigned long long *)(h->host_counters + C_KEYCOUNT);
-        uint64_t cap = 1024;
-        while (cap < 2 * nkeys + 16) cap <<= 1;
-        if (cap > (1ull << 31)) return fail(LSHB_ERR_OOM, "resolution table too large");
+        const unsigned long long *hbc = (const unsigned long long *)(h->host_counters + C_BANDCOUNT);
+        uint64_t slots = 0;
+        for (uint32_t j = 0; j < h->bands; ++j) {
+            uint64_t cap = 64;
+            while (cap < 2 * hbc[j] + 16) cap <<= 1;
+            T.seg_base[j] = slots;
+            T.seg_mask[j] = (uint32_t)(cap - 1);
+            slots += cap + 1;  // + the slot of the position 2^64 - 1
+        }
+        if (slots > (1ull << 31)) return fail(LSHB_ERR_OOM, "resolution table too large");
         lshb_status st;
-        if ((st = h->buf(B_HT_KEYS).reserve(cap * 8)) != LSHB_OK) return st;
-        if ((st = h->buf(B_HT_FIXED).reserve(cap * 4)) != LSHB_OK) return st;
-        if ((st = h->buf(B_HT_FIRST).reserve(cap * 4)) != LSHB_OK) return st;
+        if ((st = h->buf(B_HT_KEYS).reserve(slots * 8)) != LSHB_OK) return st;
+        if ((st = h->buf(B_HT_FIXED).reserve(slots * 4)) != LSHB_OK) return st;
+        if ((st = h->buf(B_HT_FIRST).reserve(slots * 4)) != LSHB_OK) return st;
         if ((st = h->buf(B_HT_SLOTS).reserve((uint64_t)nu * h->bands * h->k * 4)) != LSHB_OK) return st;
         if ((st = h->buf(B_HT_INS).reserve(nu)) != LSHB_OK) return st;
         if ((st = h->buf(B_HT_UDUP).reserve(nu)) != LSHB_OK) return st;
         T.keys = (uint64_t *)h->buf(B_HT_KEYS).ptr;
-        T.mask = (uint32_t)(cap - 1);
         T.first_fixed = (uint32_t *)h->buf(B_HT_FIXED).ptr;
         T.first = (uint32_t *)h->buf(B_HT_FIRST).ptr;
         T.slots = (uint32_t *)h->buf(B_HT_SLOTS).ptr;
         T.ins = (uint8_t *)h->buf(B_HT_INS).ptr;
         T.udup = (uint8_t *)h->buf(B_HT_UDUP).ptr;
-        T.changed = h->counters + C_CHANGED;
-        CK(cudaMemsetAsync(T.keys, 0xff, cap * 8, s));
-        CK(cudaMemsetAsync(T.first_fixed, 0xff, cap * 4, s));
+        T.ctl = h->counters + C_SWEEPCTL;
+        CK(cudaMemsetAsync(T.keys, 0xff, slots * 8, s));
+        CK(cudaMemsetAsync(T.first_fixed, 0xff, slots * 4, s));
         CK(cudaMemsetAsync(T.ins, 1, nu, s));
         CK(cudaMemsetAsync(T.udup, 0, nu, s));
+        CK(cudaMemsetAsync(T.ctl, 0, 16, s));
         CK(launch_resolve_setup(A, ulist, nu, T, h->insert_all, s));
-        const int max_sweeps = h->insert_all ? 1 : 64;
-        bool settled = false;
-        for (int it = 0; it < max_sweeps; ++it) {
-            CK(cudaMemsetAsync(T.changed, 0, 4, s));
-            CK(launch_resolve_iteration(A, ulist, nu, T, h->insert_all, s));
-            CK(cudaMemcpyAsync(h->host_counters, h->counters, 64, cudaMemcpyDeviceToHost, s));
+        // Jacobi sweeps, enqueued in growing groups; a sweep after the one
+        // that changed nothing returns at once, and the host looks once per
+        // group.  One sweep decides everything when every document inserts.
+        const uint32_t max_sweeps = h->insert_all ? 1 : 64;
+        uint32_t queued = 0, group = 2, run = 0;
+        bool done = false;
+        while (!done && queued < max_sweeps) {
+            const uint32_t g = std::min(group, max_sweeps - queued);
+            for (uint32_t i = 0; i < g; ++i)
+                CK(launch_resolve_sweep(A, ulist, nu, T, slots, h->insert_all, s));
+            queued += g;
+            group = std::min<uint32_t>(group * 2, 16);
+            CK(cudaMemcpyAsync(h->host_counters + C_SWEEPCTL, T.ctl, 16, cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
-            h->resolve_rounds++;
-            if (h->host_counters[C_CHANGED] == 0 || h->insert_all) {
-                settled = true;
-                break;
-            }
+            done = h->host_counters[C_SWEEPCTL + 1] != 0;
+            run = h->host_counters[C_SWEEPCTL + 2];
         }
-        if (!settled) {
-            CK(launch_resolve_sequential(A, ulist, nu, T, s));
+        h->resolve_rounds += run;
+        if (!done && !h->insert_all) {
+            // Not settled after max_sweeps: the first `run` uncertain
+            // documents are final; finish the rest in order.
+            CK(launch_resolve_in_order(A, ulist, nu, T, slots, std::min(run, nu), s));
             h->resolve_rounds++;
         }
     }
     unsigned long long *dupc = (unsigned long long *)(h->counters + C_DUPCOUNT);
     CK(launch_finalize_insert(A, ulist, nu, T, h->insert_all, flags_dev,
                               (uint8_t *)h->buf(B_INSD).ptr, dupc, s));
-    CK(cudaMemcpyAsync(h->host_counters, h->counters, 64, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h->host_counters, h->counters, kChunkCounterBytes, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (h->host_counters[C_ERROR] != 0)
         return fail(LSHB_ERR_CUDA, "device error word 0x%x", h->host_counters[C_ERROR]);
@@ -918,6 +938,45 @@ extern "C" lshb_status lshbloom_dedup_keys(lshbloom_t *h, const uint64_t *offset
     return run_batch_timed(h, offsets, tokens, D, flags_out, Job::Dedup, nullptr, false, keys_out);
 }
 
+extern "C" lshb_status lshbloom_dedup_from_keys(lshbloom_t *h, const uint64_t *keys, uint64_t D,
+                                                uint8_t *flags_out) {
+    if (!h) return fail(LSHB_ERR_ARG, "NULL handle");
+    if (D == 0) return LSHB_OK;
+    if (!keys || !flags_out) return fail(LSHB_ERR_ARG, "NULL pointer with D > 0");
+    const auto t0 = std::chrono::steady_clock::now();
+    std::lock_guard<std::mutex> lock(h->mu);
+    CK(cudaSetDevice(h->device));
+    const bool keys_dev = is_device_pointer(keys), out_dev = is_device_pointer(flags_out);
+    cudaStream_t s = h->stream;
+    if (keys_dev || out_dev) {
+        CK(cudaEventRecord(h->ev_order, cudaStreamLegacy));
+        CK(cudaStreamWaitEvent(s, h->ev_order, 0));
+    }
+    const uint64_t dcap = std::min<uint64_t>(D, h->max_docs_batched);
+    lshb_status st;
+    if ((st = ensure_chunk_scratch(h, dcap, 0, false, false)) != LSHB_OK) return st;
+    DevBuf &outbuf = h->buf(B_OUTSTAGE);
+    if (!out_dev && (st = outbuf.reserve(dcap)) != LSHB_OK) return st;
+    for (uint64_t lo = 0; lo < D; lo += dcap) {
+        const uint64_t Dn = std::min(dcap, D - lo);
+        CK(cudaEventRecord(h->ev_t[1], s));
+        CK(cudaMemcpyAsync(h->buf(B_KEYS).ptr, keys + lo * h->bands, Dn * h->bands * 8,
+                           keys_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        uint8_t *fl = out_dev ? flags_out + lo : (uint8_t *)outbuf.ptr;
+        if ((st = run_bloom(h, Dn, fl, s)) != LSHB_OK) return st;
+        CK(cudaEventRecord(h->ev_t[2], s));
+        if (!out_dev) CK(cudaMemcpyAsync(flags_out + lo, fl, Dn, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, h->ev_t[1], h->ev_t[2]));
+        h->t_bloom_ms += ms;
+        h->docs_seen += Dn;
+    }
+    h->t_call_ms +=
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return LSHB_OK;
+}
+
 extern "C" lshb_status lshbloom_dedup_async(lshbloom_t *h, const uint64_t *offsets,
                                             const uint32_t *tokens, uint64_t D, uint8_t *flags_out,
                                             void *stream) {
@@ -1015,11 +1074,12 @@ extern "C" lshb_status lshbloom_stats(lshbloom_t *h, lshb_stats *out) {
             CK(launch_count_occupied((const uint64_t *)f, h->words_per_filter / 2, cnt, h->stream));
         else
             CK(launch_popcount(f, h->words_per_filter, cnt, h->stream));
-        CK(cudaMemcpyAsync(h->host_counters, h->counters, 64, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(h->host_counters, h->counters, kChunkCounterBytes,
+                           cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
-        // set bits per bit, or occupied slots per slot for the exact-key tables
+        // set bits per bit, or stored keys per key slot for the exact-key tables
         out->fill[j] = (double)*(unsigned long long *)(h->host_counters + C_POPCOUNT) /
-                       (exact ? (double)(h->words_per_filter / 2) : (double)h->m);
+                       (exact ? (double)h->exact_cap : (double)h->m);
     }
     return LSHB_OK;
 }

@@ -24,20 +24,22 @@ struct DevBuf {
 
 enum BufId {
     B_KEYS, B_MISS, B_CAND, B_STATUS, B_PREHIT, B_FLAGS, B_INSD, B_ULIST, B_BLOCKCNT, B_OFFSTAGE,
-    B_SIG, B_HASHES, B_SKETCH1, B_SKETCH2, B_HT_KEYS, B_HT_FIXED, B_HT_FIRST, B_HT_SLOTS,
+    B_SIG, B_HASHES, B_SKETCH, B_HT_KEYS, B_HT_FIXED, B_HT_FIRST, B_HT_SLOTS,
     B_HT_INS, B_HT_UDUP, B_HASHOUT, B_OUTSTAGE, B_ITEMS, B_PENDING, B_NBUF
 };
 
-// Slots of the small device counter block (uint32 units).
+// Slots of the device counter block (uint32 units; kCounterBytes in all).
 enum CounterId {
     C_NU = 0,         // uncertain documents of the chunk
-    C_CHANGED = 1,    // a resolution sweep changed an insert decision
     C_ERROR = 2,      // device error bits
-    C_KEYCOUNT = 4,   // (u64) candidate bits of uncertain documents
     C_DUPCOUNT = 6,   // (u64) duplicates of the chunk
     C_POPCOUNT = 8,   // (u64) popcount scratch
-    C_QUEUE = 10      // (u64) batched work-queue head
+    C_QUEUE = 10,     // (u64) batched work-queue head
+    C_SWEEPCTL = 12,  // 4 words: sweep changed, sweeps done, sweeps run, scratch
+    C_BANDCOUNT = 64  // (u64 x 64) candidate bits of uncertain documents per band
 };
+constexpr size_t kCounterBytes = 1024;
+constexpr size_t kChunkCounterBytes = 64;  // C_NU .. C_SWEEPCTL: cleared per chunk
 
 struct SigPass {
     uint32_t p0, npc;
@@ -65,6 +67,7 @@ struct lshbloom {
     uint32_t layout = 0;   // 0 standard, 1 blocked, 2 exact key sets
     double p = 0.0;
     uint64_t m = 0, words_per_filter = 0;
+    uint64_t exact_cap = 0;  // exact layout: key slots per band table (power of two)
     std::vector<uint64_t> a, b;
     std::vector<lshb::SigPass> passes;
     uint32_t *filters = nullptr;
@@ -77,12 +80,11 @@ struct lshbloom {
     uint64_t h2d_bytes = 0, host_read_bytes = 0;
     bool pageable_access = false;  // the device reads pageable host memory via host page tables
     lshb::DevBuf stage_tok[2];
-    uint32_t *counters = nullptr;       // device, 64 x uint32
+    uint32_t *counters = nullptr;       // device, kCounterBytes
     uint32_t *host_counters = nullptr;  // pinned mirror
     lshb::DevBuf bufs[lshb::B_NBUF];
     uint64_t max_docs = 0, max_tokens = 0;
     uint64_t max_docs_batched = 0, max_tokens_batched = 0;
-    uint32_t sketch_log2_cap = 0;
     uint32_t item_shingles = 0;
     lshb::BatchedState *batched = nullptr;
     uint64_t docs_seen = 0, dups_seen = 0, resolve_rounds = 0, uncertain_docs = 0;
@@ -126,7 +128,12 @@ lshb_status ensure_chunk_scratch(lshbloom *h, uint64_t Dc, uint64_t Tc, bool pla
 lshb_status ensure_stage(lshbloom *h, uint64_t Tc);
 lshb_status run_signatures(lshbloom *h, const ChunkIn &in, uint32_t *sig_out, uint32_t *hash_out,
                            bool want_keys, cudaStream_t s);
-BloomArgs bloom_args(lshbloom *h, uint64_t D);
+// Sketch cells per band for batches of up to dcap documents.
+uint64_t sketch_cells_for(const lshbloom *h, uint64_t dcap);
+// Bloom-stage arguments for a batch of D documents in scratch sized for dcap.
+BloomArgs bloom_args(lshbloom *h, uint64_t D, uint64_t dcap);
+// Probe sectors one band key addresses (k, or one block / one key).
+uint64_t probe_sectors_per_key(const lshbloom *h);
 lshb_status run_bloom(lshbloom *h, uint64_t D, uint8_t *flags_dev, cudaStream_t s);
 lshb_status resolve_and_insert(lshbloom *h, const BloomArgs &A, uint8_t *flags_dev,
                                cudaStream_t s);

@@ -360,10 +360,10 @@ def test_exact_key_index(lshb, oracle, corpus, exec_mode):
     want = ref.dedup(off, tok)
     assert np.array_equal(got, want)
     for j in range(11):
-        table = ix.filter_bytes(j).view(np.uint64)
-        assert np.array_equal(np.sort(table[table != np.uint64(2**64 - 1)]), ref.exact_keys(j))
+        assert np.array_equal(ix.exact_keys(j), ref.exact_keys(j))
     st = ix.stats()
-    assert st["k"] == 1 and st["filter_bytes"] == 4096 * 8
+    # 4096 key slots, the slot of the key 2^64-1 and 15 padding slots
+    assert st["k"] == 1 and st["filter_bytes"] == (4096 + 16) * 8
 
 
 @pytest.mark.parametrize("ngram", [1, 7])
@@ -489,7 +489,53 @@ def test_option_combinations(lshb, oracle, corpus, layout, band_key, insert_all,
     for j in (0, 5, 10):
         fb = ix.filter_bytes(j)
         if layout == "exact":
-            t = fb.view(np.uint64)
-            assert np.array_equal(np.sort(t[t != np.uint64(2**64 - 1)]), ref.exact_keys(j))
+            assert np.array_equal(ix.exact_keys(j), ref.exact_keys(j))
         else:
             assert np.array_equal(fb, ref.filter_bytes(j))
+
+
+def _chain_keys(n, bands=4):
+    """Document i shares one band key with document i-1 only (band 0 and band 1
+    alternately): under the insert-non-duplicates rule every decision depends
+    on the previous one, a chain of n documents."""
+    i = np.arange(n, dtype=np.uint64)
+    keys = np.zeros((n, bands), np.uint64)
+    keys[:, 0] = (i + np.uint64(1)) // np.uint64(2)
+    keys[:, 1] = i // np.uint64(2) + np.uint64(10**6)
+    for j in range(2, bands):
+        keys[:, j] = i * np.uint64(bands) + np.uint64(j) + np.uint64(10**9)
+    return keys
+
+
+@pytest.mark.parametrize("layout,lay", [("standard", 0), ("blocked", 1), ("exact", 2)])
+@pytest.mark.parametrize("insert_all", [False, True])
+def test_dedup_from_keys_matches_oracle(lshb, oracle, layout, lay, insert_all):
+    """lshbloom_dedup_from_keys on arbitrary 64-bit band keys: equal keys, keys
+    a multiple of 2^58 apart in one band and across bands, 2^64 - 1, and a
+    2,000-document dependency chain (more than the 64 Jacobi sweeps, so the
+    in-order finish runs), in chunks of 1,000 documents, from host and device
+    memory; flags and the final index equal the oracle's replay of the keys."""
+    from test_oracle_exact_keys import constructed, random_keys
+    keys = np.concatenate([constructed(), random_keys(3000, 9), _chain_keys(2000)])
+    kw = dict(n_expected=6000, fp_rate=1e-3, insert_all=insert_all)
+    ix = lshb.LSHBloom(8, 4, 2, bloom_layout=layout, max_batch_docs=1000, **kw)
+    ref = oracle.OracleIndex(8, 4, 2, layout=lay, **kw)
+    assert (ix.m, ix.k) == (ref.m, ref.k) or layout == "exact"
+    got = np.concatenate([
+        np.asarray(ix.dedup_from_keys(keys[:8])),
+        ix.dedup_from_keys(torch.from_numpy(keys[8:2500].view(np.int64)).cuda()).cpu().numpy(),
+        np.asarray(ix.dedup_from_keys(keys[2500:]))])
+    want = ref.dedup_keys(keys)
+    diff = np.nonzero(got != want)[0]
+    assert diff.size == 0, diff[:10]
+    assert 0 < want.sum() < want.size
+    for j in range(4):
+        if layout == "exact":
+            assert np.array_equal(ix.exact_keys(j), ref.exact_keys(j))
+        else:
+            assert np.array_equal(ix.filter_bytes(j), ref.filter_bytes(j))
+    st = ix.stats()
+    assert st["docs_seen"] == keys.shape[0]
+    if not insert_all:
+        assert st["resolve_rounds"] > 64          # the chain outlasted the sweeps
+    ix.close()
