@@ -4,9 +4,13 @@
 // soon as an in-flight slot and enough of the device-memory budget are free,
 // and enqueues its copy-in and its signature stage on a stream of its own, so
 // every admitted request computes at the same time as the others.  The Bloom
-// stage of an index then runs, in arrival order, for each request of that
-// index whose signatures are done: each request is judged against exactly the
-// requests submitted before it to the same index (Sec. 2.1, Sec. 4.4.2).
+// stage of an index then runs, in arrival order, over the longest run of that
+// index's oldest requests whose signatures are done: their band keys are laid
+// end to end and judged as one batch, which is the same as judging the
+// requests one after the other (Sec. 2.1, Sec. 4.4.2), so each request is
+// judged against exactly the requests submitted before it to the same index,
+// while the Bloom stage's fixed costs (a few kernel launches and host round
+// trips) are paid once per group instead of once per request.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -119,8 +123,12 @@ struct lshbloom_server {
 
     void loop();
     lshb_status launch(Request *r);
-    lshb_status bloom(Request *r);
+    lshb_status bloom(const std::vector<Request *> &group);
 };
+
+// Documents of one grouped Bloom stage at most (a group always takes at least
+// its first request).
+constexpr uint64_t kMaxGroupDocs = 1ull << 20;
 
 // Budget of a request: its keys and flags, and the offsets and tokens that
 // are copied rather than read in place.
@@ -176,21 +184,35 @@ lshb_status lshbloom_server::launch(Request *r) {
     return LSHB_OK;
 }
 
-// Bloom stage of one request on its index (the worker thread only).
-lshb_status lshbloom_server::bloom(Request *r) {
-    lshbloom *h = idx[r->index];
+// Bloom stage of a group of requests of one index, in arrival order, as one
+// batch (the worker thread only).
+lshb_status lshbloom_server::bloom(const std::vector<Request *> &group) {
+    lshbloom *h = idx[group.front()->index];
     std::lock_guard<std::mutex> lock(h->mu);
-    lshb_status st = ensure_chunk_scratch(h, r->D, 0, false, false);
+    uint64_t D = 0;
+    for (Request *r : group) D += r->D;
+    lshb_status st = ensure_chunk_scratch(h, D, 0, false, false);
     if (st != LSHB_OK) return st;
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(h->buf(B_KEYS).ptr, r->d_keys, r->D * h->bands * 8, cudaMemcpyDeviceToDevice,
-                             h->stream)) != cudaSuccess)
-        return cuda_fail(e, "keys");
-    if ((st = run_bloom(h, r->D, r->d_flags, h->stream)) != LSHB_OK) return st;
-    if ((e = cudaMemcpyAsync(r->h_flags, r->d_flags, r->D, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
-        return cuda_fail(e, "flags");
+    uint64_t *keys = (uint64_t *)h->buf(B_KEYS).ptr;
+    uint64_t at = 0;
+    for (Request *r : group) {
+        if ((e = cudaMemcpyAsync(keys + at * h->bands, r->d_keys, r->D * h->bands * 8,
+                                 cudaMemcpyDeviceToDevice, h->stream)) != cudaSuccess)
+            return cuda_fail(e, "keys");
+        at += r->D;
+    }
+    uint8_t *flags = (uint8_t *)h->buf(B_FLAGS).ptr;
+    if ((st = run_bloom(h, D, flags, h->stream)) != LSHB_OK) return st;
+    at = 0;
+    for (Request *r : group) {
+        if ((e = cudaMemcpyAsync(r->h_flags, flags + at, r->D, cudaMemcpyDeviceToHost, h->stream)) !=
+            cudaSuccess)
+            return cuda_fail(e, "flags");
+        at += r->D;
+    }
     if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(e, "sync");
-    h->docs_seen += r->D;
+    h->docs_seen += D;
     return LSHB_OK;
 }
 
@@ -220,27 +242,40 @@ void lshbloom_server::loop() {
             lshb_status st = launch(r);
             if (st != LSHB_OK) r->status = st;
         }
-        // Bloom stage, per index in arrival order, for finished signature stages
+        // Bloom stage, per index in arrival order: the oldest requests whose
+        // signature stages are done, as one group
         std::vector<Request *> finished;
         for (size_t i = 0; i < running.size(); ++i) {
             for (;;) {
-                Request *r = nullptr;
+                std::vector<Request *> group;
+                uint64_t docs = 0;
                 {
                     std::lock_guard<std::mutex> g(mu);
-                    if (running[i].empty()) break;
-                    r = running[i].front();
+                    for (Request *r : running[i]) {
+                        if (!group.empty() && docs + r->D > kMaxGroupDocs) break;
+                        if (r->status == LSHB_OK) {
+                            const cudaError_t q = cudaEventQuery(events[r->slot]);
+                            if (q == cudaErrorNotReady) break;
+                            if (q != cudaSuccess) r->status = cuda_fail(q, "signature stage");
+                        }
+                        if (r->status != LSHB_OK) {
+                            if (group.empty()) group.push_back(r);  // fails alone
+                            break;
+                        }
+                        group.push_back(r);
+                        docs += r->D;
+                    }
                 }
-                if (r->status == LSHB_OK) {
-                    const cudaError_t q = cudaEventQuery(events[r->slot]);
-                    if (q == cudaErrorNotReady) break;
-                    if (q != cudaSuccess) r->status = cuda_fail(q, "signature stage");
-                    else r->status = bloom(r);
+                if (group.empty()) break;
+                if (group.front()->status != LSHB_OK) {
+                    cudaStreamSynchronize(streams[group.front()->slot]);
                 } else {
-                    cudaStreamSynchronize(streams[r->slot]);
+                    const lshb_status st = bloom(group);
+                    for (Request *r : group) r->status = st;
                 }
                 std::lock_guard<std::mutex> g(mu);
-                running[i].pop_front();
-                finished.push_back(r);
+                for (size_t k = 0; k < group.size(); ++k) running[i].pop_front();
+                finished.insert(finished.end(), group.begin(), group.end());
             }
         }
         lk.lock();
