@@ -113,7 +113,10 @@ __device__ __forceinline__ bool exact_insert(uint64_t *T, uint64_t cap, uint64_t
 
 // Probe one band key against its filter F (pre-batch bits): the mask of
 // probes that found a clear bit; each such position is marked in the band's
-// sketch.  For k <= KMAX all k loads are issued before any is used.
+// sketch.  For k <= KMAX all k loads are issued before any is used, then all
+// first-level marks, then the second level: one memory round trip per phase
+// instead of one per probe (positions are recomputed per phase: a few integer
+// operations, fewer registers).
 template <int KMAX>
 __device__ __forceinline__ uint64_t probe_key(const BloomArgs &A, uint32_t j, uint64_t key) {
     const uint32_t *F = A.filters + (uint64_t)j * A.words_per_filter;
@@ -132,6 +135,24 @@ __device__ __forceinline__ uint64_t probe_key(const BloomArgs &A, uint32_t j, ui
 #pragma unroll
         for (int u = 0; u < KMAX; ++u)
             if (!((w[u] >> (ps.pos(u) & 31)) & 1u)) miss |= 1ull << u;
+        uint32_t *S = A.sketch + (uint64_t)j * (A.sketch_cells >> 4);
+#pragma unroll
+        for (int u = 0; u < KMAX; ++u) {
+            w[u] = 0;
+            if ((miss >> u) & 1ull) {
+                const uint64_t c = sketch_cell(ps.pos(u), A.sketch_cells);
+                w[u] = atomicOr(S + (c >> 4), 1u << (2u * (uint32_t)(c & 15)));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < KMAX; ++u) {
+            if ((miss >> u) & 1ull) {
+                const uint64_t c = sketch_cell(ps.pos(u), A.sketch_cells);
+                const uint32_t sh = 2u * (uint32_t)(c & 15);
+                if ((w[u] >> sh) & 1u) atomicOr(S + (c >> 4), 2u << sh);
+            }
+        }
+        return miss;
     } else {
         for (uint32_t u0 = 0; u0 < A.k; u0 += 8) {
             uint32_t w[8];
