@@ -620,12 +620,16 @@ lshb_status lshb::run_signatures(lshbloom *h, const ChunkIn &in, uint32_t *sig_o
     return LSHB_OK;
 }
 
-// Two cells per possible mark (b k per document and band): a missing bit of
+// Two cells per possible mark (k per document and band): a missing bit of
 // one document is then marked by another unrelated one with probability
 // 1 - e^(-1/2), and all k = 17 missing bits of a band (a false candidate)
-// with probability about 1e-7.
+// with probability about 1e-7.  With k <= 2 (the exact key sets: one
+// "position" per band) that rate would make nearly every document uncertain,
+// so those take 64 cells per document and band (a false candidate per band
+// with probability about 1/64).
 uint64_t lshb::sketch_cells_for(const lshbloom *h, uint64_t dcap) {
-    const uint64_t cells = std::max<uint64_t>(2 * std::max<uint64_t>(dcap, 1) * h->k, 1024);
+    const uint64_t per_doc = h->k <= 2 ? 64 : 2 * (uint64_t)h->k;
+    const uint64_t cells = std::max<uint64_t>(per_doc * std::max<uint64_t>(dcap, 1), 1024);
     return (cells + 15) / 16 * 16;
 }
 
