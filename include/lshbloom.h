@@ -321,18 +321,25 @@ LSHB_API lshb_status lshbloom_filter_sizing(uint64_t n_expected, double fp_rate,
  *
  * A server owns a device-memory budget and a worker thread.  Requests (CSR
  * batches for one of its indexes) are admitted in arrival order as soon as an
- * in-flight slot and enough of the budget are free; the copy-in and the
- * signature stage of every admitted request run at once on separate streams,
- * so requests that arrive while others are on the GPU join them there.  The
- * Bloom stage of each index runs in arrival order, so every request is judged
- * against exactly the documents submitted before it to the same index
- * (Sec. 2.1): its flags equal those of lshbloom_dedup calls made one after
- * the other in submission order.  The filters stay resident across requests. */
+ * in-flight slot and enough of the budget are free.  Each index has a stream
+ * for signatures: whenever its previous launch is done, all its admitted
+ * requests not yet started go into one launch of the persistent signature
+ * kernel (one work queue over their documents, long documents split), so
+ * requests that arrive while others are on the GPU join the next launch, and
+ * the indexes' launches overlap.  The Bloom stage of each index runs in
+ * arrival order, over the run of its oldest requests whose keys are ready,
+ * as one batch, so every request is judged against exactly the documents
+ * submitted before it to the same index (Sec. 2.1): its flags equal those of
+ * lshbloom_dedup calls made one after the other in submission order.  The
+ * filters stay resident across requests. */
 typedef struct lshbloom_server lshbloom_server_t;
 
 /* indexes: n handles (same device; P <= 256) that the server uses exclusively
  * until destroyed.  mem_budget_bytes: device memory for in-flight requests
- * (tokens, offsets, keys, flags), allocated once here.  max_inflight: at most
+ * (the keys of each, and the offsets and tokens the GPU cannot read in place),
+ * allocated once here; each index's signature launches also keep scratch of
+ * their own (work-item lists and merged signature rows of split documents,
+ * grown to the largest launch, at most 2^18 documents).  max_inflight: at most
  * this many admitted requests (1..256).  Errors: ERR_ARG, ERR_OOM, ERR_CUDA. */
 LSHB_API lshb_status lshbloom_server_create(lshbloom_t *const *indexes, uint32_t n,
                                             uint64_t mem_budget_bytes, uint32_t max_inflight,

@@ -145,17 +145,9 @@ static BatchArgs make_args(lshbloom *h, BatchedState *b) {
     return a;
 }
 
-// Everything before the host-side resolution, for the chunk described by the
-// device parameter block (enqueued on s; also what the graph captures).
-static lshb_status enqueue_front(lshbloom *h, BatchedState *b, BatchArgs a, bool with_bloom,
-                                 cudaStream_t s, bool time_kernel) {
-    const uint64_t dcap = b->dcap;
-    BloomArgs A = bloom_args(h, dcap, dcap);
-    A.D_dev = &b->dyn->D;
-    BCK(cudaMemcpyAsync(b->dyn, b->dyn_host, sizeof(DynParams), cudaMemcpyHostToDevice, s));
-    BCK(cudaMemsetAsync(h->counters, 0, kChunkCounterBytes, s));
-    if (with_bloom)
-        BCK(cudaMemsetAsync(A.sketch, 0, (uint64_t)h->bands * (A.sketch_cells / 16) * 4, s));
+// Per-document item counts, their scan and the item -> document map for a
+// launch of up to dcap documents described by a.dyn.
+static cudaError_t enqueue_items(const BatchArgs &a, uint64_t dcap, cudaStream_t s) {
     const unsigned nb = (unsigned)((dcap + kScanBlock - 1) / kScanBlock);
     unsigned pg = (unsigned)std::min<uint64_t>((dcap + 255) / 256, 16384);
     k_batch_prepare<<<pg ? pg : 1, 256, 0, s>>>(a);
@@ -168,7 +160,21 @@ static lshb_status enqueue_front(lshbloom *h, BatchedState *b, BatchArgs a, bool
     count_launch();
     k_expand<<<pg ? pg : 1, 256, 0, s>>>(a);
     count_launch();
-    BCK(cudaGetLastError());
+    return cudaGetLastError();
+}
+
+// Everything before the host-side resolution, for the chunk described by the
+// device parameter block (enqueued on s; also what the graph captures).
+static lshb_status enqueue_front(lshbloom *h, BatchedState *b, BatchArgs a, bool with_bloom,
+                                 cudaStream_t s, bool time_kernel) {
+    const uint64_t dcap = b->dcap;
+    BloomArgs A = bloom_args(h, dcap, dcap);
+    A.D_dev = &b->dyn->D;
+    BCK(cudaMemcpyAsync(b->dyn, b->dyn_host, sizeof(DynParams), cudaMemcpyHostToDevice, s));
+    BCK(cudaMemsetAsync(h->counters, 0, kChunkCounterBytes, s));
+    if (with_bloom)
+        BCK(cudaMemsetAsync(A.sketch, 0, (uint64_t)h->bands * (A.sketch_cells / 16) * 4, s));
+    BCK(enqueue_items(a, dcap, s));
     // Under capture the records must be external to become event-record nodes
     // of the graph (then every replay times the persistent kernel).
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -314,8 +320,8 @@ lshb_status run_batched(lshbloom *h, const uint64_t *offsets, const uint32_t *to
     for (size_t ci = 0; ci < chunks.size(); ++ci) {
         const uint64_t lo = chunks[ci].first, hi = chunks[ci].second, Dn = hi - lo;
         DynParams dp;
+        memset(&dp, 0, sizeof dp);
         dp.D = Dn;
-        dp.n_items = 0;
         if (off_dev) {
             dp.offsets = offsets + lo;
         } else {
@@ -375,6 +381,98 @@ lshb_status run_batched(lshbloom *h, const uint64_t *offsets, const uint32_t *to
         h->docs_seen += Dn;
     }
     BCK(cudaStreamSynchronize(s));
+    return LSHB_OK;
+}
+
+// ---- several CSR batches in one launch (the server's signature stage) ---------------
+
+struct SegmentState {
+    uint64_t dcap = 0, item_cap = 0;
+    int grid = 0;
+    DynParams *dyn = nullptr, *dyn_host = nullptr;       // device / pinned
+    Segment *segs = nullptr, *segs_host = nullptr;       // device / pinned, kMaxSegments
+    unsigned long long *queue = nullptr;                 // device work-queue head
+    uint32_t *error = nullptr, *error_host = nullptr;    // device / pinned error word
+    DevBuf item_count, item_start, block_sums, item_doc, pending, sig_partial;
+
+    ~SegmentState() {
+        item_count.release(); item_start.release(); block_sums.release();
+        item_doc.release(); pending.release(); sig_partial.release();
+        if (dyn) cudaFree(dyn);
+        if (segs) cudaFree(segs);
+        if (queue) cudaFree(queue);
+        if (error) cudaFree(error);
+        if (dyn_host) cudaFreeHost(dyn_host);
+        if (segs_host) cudaFreeHost(segs_host);
+        if (error_host) cudaFreeHost(error_host);
+    }
+};
+
+SegmentState *segment_state_create() { return new (std::nothrow) SegmentState(); }
+void segment_state_destroy(SegmentState *st) { delete st; }
+uint32_t segment_state_error(const SegmentState *st) { return st->error_host ? *st->error_host : 0u; }
+
+lshb_status launch_keys_segments(lshbloom *h, SegmentState *st, const Segment *segs,
+                                 uint32_t nseg, uint64_t D, uint64_t T, cudaStream_t s) {
+    if (nseg == 0 || nseg > kMaxSegments || D == 0)
+        return fail(LSHB_ERR_ARG, "segment launch of %u batches, %llu documents", nseg,
+                    (unsigned long long)D);
+    if (!st->dyn) {
+        BCK(cudaMalloc(&st->dyn, sizeof(DynParams)));
+        BCK(cudaMalloc(&st->segs, sizeof(Segment) * kMaxSegments));
+        BCK(cudaMalloc(&st->queue, 8));
+        BCK(cudaMalloc(&st->error, 4));
+        BCK(cudaMemset(st->error, 0, 4));
+        BCK(cudaMallocHost(&st->dyn_host, sizeof(DynParams)));
+        BCK(cudaMallocHost(&st->segs_host, sizeof(Segment) * kMaxSegments));
+        BCK(cudaMallocHost(&st->error_host, 4));
+        *st->error_host = 0;
+    }
+    const uint32_t item = h->cfg.item_shingles ? h->cfg.item_shingles : 512u;
+    st->dcap = std::max(st->dcap, D);
+    st->item_cap = std::max(st->item_cap, T / kItemCandidates[0] + D + 1);
+    lshb_status r;
+    if ((r = st->item_count.reserve(st->dcap * 4)) != LSHB_OK) return r;
+    if ((r = st->item_start.reserve((st->dcap + 1) * 8)) != LSHB_OK) return r;
+    if ((r = st->block_sums.reserve(((st->dcap + kScanBlock - 1) / kScanBlock + 1) * 8)) != LSHB_OK)
+        return r;
+    if ((r = st->item_doc.reserve(st->item_cap * 4)) != LSHB_OK) return r;
+    if ((r = st->pending.reserve(st->dcap * 4)) != LSHB_OK) return r;
+    if ((r = st->sig_partial.reserve(st->dcap * h->P * 4)) != LSHB_OK) return r;
+    if (!st->grid) st->grid = batched_grid(ngram_template(h->ngram), h->passes[0].ppl);
+    // the pinned blocks are free: the previous launch of this state is complete
+    memcpy(st->segs_host, segs, sizeof(Segment) * nseg);
+    memset(st->dyn_host, 0, sizeof(DynParams));
+    st->dyn_host->D = D;
+    st->dyn_host->segs = st->segs;
+    st->dyn_host->nseg = nseg;
+    BatchArgs a;
+    memset(&a, 0, sizeof a);
+    const SigPass &ps = h->passes[0];
+    a.dyn = st->dyn;
+    a.item_shingles = item;
+    a.ngram = h->ngram;
+    a.P = h->P;
+    a.npc = ps.npc;
+    a.bands = h->bands;
+    a.rows = h->rows;
+    a.band_key = h->cfg.band_key;
+    a.item_count = (uint32_t *)st->item_count.ptr;
+    a.item_start = (uint64_t *)st->item_start.ptr;
+    a.block_sums = (uint64_t *)st->block_sums.ptr;
+    a.item_doc = (uint32_t *)st->item_doc.ptr;
+    a.item_cap = st->item_cap;
+    a.pending = (uint32_t *)st->pending.ptr;
+    a.sig_partial = (uint32_t *)st->sig_partial.ptr;
+    a.queue = st->queue;
+    a.error = st->error;
+    a.c = ps.c;
+    BCK(cudaMemcpyAsync(st->segs, st->segs_host, sizeof(Segment) * nseg, cudaMemcpyHostToDevice, s));
+    BCK(cudaMemcpyAsync(st->dyn, st->dyn_host, sizeof(DynParams), cudaMemcpyHostToDevice, s));
+    BCK(cudaMemsetAsync(st->queue, 0, 8, s));
+    BCK(enqueue_items(a, D, s));
+    BCK(launch_k_batched(ngram_template(h->ngram), ps.ppl, a, st->grid, s));
+    BCK(cudaMemcpyAsync(st->error_host, st->error, 4, cudaMemcpyDeviceToHost, s));
     return LSHB_OK;
 }
 

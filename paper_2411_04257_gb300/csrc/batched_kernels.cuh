@@ -6,6 +6,7 @@
 
 #include "bloom_kernels.cuh"
 #include "lshb_internal.h"
+#include "segment.h"
 #include "sig_kernels.cuh"
 
 namespace lshb {
@@ -19,7 +20,43 @@ struct DynParams {
     uint64_t tok_base;
     uint64_t D;
     uint64_t n_items;         // written on the device by the scan
+    const Segment *segs;      // nseg > 0: the launch covers these batches instead
+    uint32_t nseg;
 };
+
+// Where document d of a launch lives: its offsets (indexed by `local`), its
+// token base and the row of its band keys.
+struct DocRef {
+    const uint64_t *offsets;
+    const uint32_t *tokens;
+    uint64_t tok_base, local;
+    uint64_t *keys;
+};
+
+__device__ __forceinline__ DocRef doc_ref(const DynParams &dp, uint64_t *keys, uint32_t bands,
+                                          uint64_t d) {
+    DocRef r;
+    if (dp.nseg == 0) {
+        r.offsets = dp.offsets;
+        r.tokens = dp.tokens;
+        r.tok_base = dp.tok_base;
+        r.local = d;
+        r.keys = keys + d * bands;
+        return r;
+    }
+    uint32_t lo = 0, hi = dp.nseg - 1;  // last segment with doc0 <= d
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (dp.segs[mid].doc0 <= d) lo = mid; else hi = mid - 1;
+    }
+    const Segment &sg = dp.segs[lo];
+    r.offsets = sg.offsets;
+    r.tokens = sg.tokens;
+    r.tok_base = sg.tok_base;
+    r.local = d - sg.doc0;
+    r.keys = sg.keys_out + r.local * bands;
+    return r;
+}
 
 struct BatchArgs {
     DynParams *dyn;
@@ -32,9 +69,9 @@ struct BatchArgs {
     uint32_t *pending;         // D: items of the document not finished yet
     uint32_t *sig_partial;     // D x P: merged minima of split documents
     unsigned long long *queue;
-    uint64_t *keys;            // D x bands
-    uint64_t *cand;            // D: cleared for the Bloom stage
-    uint8_t *prehit;           // D: cleared for the Bloom stage
+    uint64_t *keys;            // D x bands (single-batch launches)
+    uint64_t *cand;            // D: cleared for the Bloom stage (nullptr: left alone)
+    uint8_t *prehit;           // D: cleared for the Bloom stage (nullptr: left alone)
     uint32_t *error;
     PermSlice c;
 };
@@ -50,12 +87,13 @@ __global__ void k_batch_prepare(const __grid_constant__ BatchArgs A) {
     const DynParams dp = *A.dyn;
     for (uint64_t d = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; d < dp.D;
          d += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t L = dp.offsets[d + 1] - dp.offsets[d];
+        const DocRef r = doc_ref(dp, A.keys, A.bands, d);
+        const uint64_t L = r.offsets[r.local + 1] - r.offsets[r.local];
         const uint64_t it = items_of(L, A.ngram, A.item_shingles);
         A.item_count[d] = (uint32_t)it;
         A.pending[d] = (uint32_t)it;
-        A.cand[d] = 0;
-        A.prehit[d] = 0;
+        if (A.cand) A.cand[d] = 0;
+        if (A.prehit) A.prehit[d] = 0;
         if (it > 1) {
             uint32_t *row = A.sig_partial + d * A.P;
             for (uint32_t p = 0; p < A.P; ++p) row[p] = 0xffffffffu;
@@ -165,9 +203,10 @@ __global__ void __launch_bounds__(kBatchThreads) k_batched(const __grid_constant
             if (lane == 0) atomicOr(A.error, kErrQueue);
             continue;
         }
-        const uint64_t o0 = dp.offsets[d];
-        const uint64_t L = dp.offsets[d + 1] - o0;
-        const uint32_t *tk = dp.tokens + (o0 - dp.tok_base);
+        const DocRef r = doc_ref(dp, A.keys, A.bands, d);
+        const uint64_t o0 = r.offsets[r.local];
+        const uint64_t L = r.offsets[r.local + 1] - o0;
+        const uint32_t *tk = r.tokens + (o0 - r.tok_base);
         const uint64_t S = shingle_count(L, n);
         const uint64_t s_begin = (it - ibeg) * A.item_shingles;
         const uint64_t s_end = min(S, s_begin + A.item_shingles);
@@ -195,7 +234,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batched(const __grid_constant
         for (int t = 0; t < PPL; ++t) sigbuf[lane + 32 * t] = mn[t];
         __syncwarp();
         for (uint32_t j = lane; j < A.bands; j += 32)
-            A.keys[d * A.bands + j] = band_key_of(sigbuf + j * A.rows, A.rows, j, A.band_key);
+            r.keys[j] = band_key_of(sigbuf + j * A.rows, A.rows, j, A.band_key);
         __syncwarp();
     }
 }

@@ -138,6 +138,21 @@ lshb_status run_bloom(lshbloom *h, uint64_t D, uint8_t *flags_dev, cudaStream_t 
 lshb_status resolve_and_insert(lshbloom *h, const BloomArgs &A, uint8_t *flags_dev,
                                cudaStream_t s);
 
+// Several CSR batches in one launch of the persistent kernel (batched.cu):
+// their band keys, written to each batch's keys_out.  The state keeps the
+// launch's scratch; the caller starts a launch only once the previous launch
+// of the same state has completed on the GPU.
+struct Segment;  // segment.h
+struct SegmentState;
+constexpr uint32_t kMaxSegments = 256;
+SegmentState *segment_state_create();
+void segment_state_destroy(SegmentState *st);
+// The launch's device error word as copied back at its end (valid once the
+// launch has completed); nonzero = work-queue inconsistency.
+uint32_t segment_state_error(const SegmentState *st);
+lshb_status launch_keys_segments(lshbloom *h, SegmentState *st, const Segment *segs,
+                                 uint32_t nseg, uint64_t D, uint64_t T, cudaStream_t s);
+
 // Batched (persistent, graph-launched) form.
 lshb_status run_batched(lshbloom *h, const uint64_t *offsets, const uint32_t *tokens, uint64_t D,
                         uint8_t *flags, const std::vector<uint64_t> &off, bool off_dev,

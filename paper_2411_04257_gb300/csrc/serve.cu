@@ -1,9 +1,13 @@
 // Serving: a request server with continuous batching over resident indexes.
 //
 // Requests wait in one FIFO.  A worker thread admits the head of the FIFO as
-// soon as an in-flight slot and enough of the device-memory budget are free,
-// and enqueues its copy-in and its signature stage on a stream of its own, so
-// every admitted request computes at the same time as the others.  The Bloom
+// soon as an in-flight slot and enough of the device-memory budget are free.
+// Each index has a signature stream: whenever its previous launch is done,
+// every admitted request of that index not yet started goes into one launch
+// of the persistent kernel (one work queue of (document, shingle range) items
+// over all of them, long documents split), after the copy-in of whatever the
+// GPU cannot read in place; the indexes' launches run at the same time, and
+// requests that arrive while a launch computes join the next one.  The Bloom
 // stage of an index then runs, in arrival order, over the longest run of that
 // index's oldest requests whose signatures are done: their band keys are laid
 // end to end and judged as one batch, which is the same as judging the
@@ -25,7 +29,7 @@
 #include <vector>
 
 #include "runtime_internal.h"
-#include "sig_kernels.cuh"
+#include "segment.h"
 
 using namespace lshb;
 
@@ -48,8 +52,8 @@ struct Request {
     uint64_t *d_off = nullptr;
     uint32_t *d_tok = nullptr;
     uint64_t *d_keys = nullptr;
-    uint8_t *d_flags = nullptr;
     int slot = -1;
+    bool keyed = false;  // band keys are in d_keys
     RState state = RState::Pending;
     lshb_status status = LSHB_OK;
     Clock::time_point t_submit, t_done;
@@ -109,11 +113,16 @@ struct lshbloom_server {
     bool stage_inputs = false;     // an index asked for staged host inputs
     Pool pool;
     void *pool_mem = nullptr;
-    std::vector<cudaStream_t> streams;
-    std::vector<cudaEvent_t> events;
     std::vector<int> free_slots;
     std::deque<Request *> fifo;
     std::vector<std::deque<Request *>> running;  // per index, arrival order
+    // per index: the signature stream, its launch state, the admitted
+    // requests not yet launched and those of the launch in flight
+    std::vector<cudaStream_t> sig_stream;
+    std::vector<cudaEvent_t> sig_event;
+    std::vector<SegmentState *> seg;
+    std::vector<std::deque<Request *>> sig_wait;
+    std::vector<std::vector<Request *>> sig_flight;
     std::unordered_map<uint64_t, Request *> reqs;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -122,66 +131,77 @@ struct lshbloom_server {
     uint64_t next_ticket = 1;
 
     void loop();
-    lshb_status launch(Request *r);
+    void launch(uint32_t i);
     lshb_status bloom(const std::vector<Request *> &group);
 };
+
+// Documents and batches of one signature launch at most.
+constexpr uint64_t kMaxLaunchDocs = 1ull << 18;
 
 // Documents of one grouped Bloom stage at most (a group always takes at least
 // its first request).
 constexpr uint64_t kMaxGroupDocs = 1ull << 20;
 
-// Budget of a request: its keys and flags, and the offsets and tokens that
-// are copied rather than read in place.
+// Budget of a request: its keys, and the offsets and tokens that are copied
+// rather than read in place.
 static uint64_t request_bytes(uint64_t D, uint64_t T, uint32_t bands, bool copy_off, bool copy_tok) {
     return (copy_off ? align256((D + 1) * 8) : 0) + (copy_tok ? align256(T * 4) : 0) +
-           align256(D * bands * 8) + align256(D);
+           align256(D * bands * 8);
 }
 
-lshb_status lshbloom_server::launch(Request *r) {
-    cudaStream_t s = streams[r->slot];
-    uint8_t *p = pool.base + r->pool_off;
-    cudaError_t e;
-    if (!r->in_off) {
-        r->d_off = (uint64_t *)p;
-        p += align256((r->D + 1) * 8);
-        if ((e = cudaMemcpyAsync(r->d_off, r->h_off, (r->D + 1) * 8, cudaMemcpyHostToDevice, s)) !=
-            cudaSuccess)
-            return cuda_fail(e, "request offsets");
+// One signature launch for index i: the oldest admitted requests not yet
+// started, up to kMaxLaunchDocs documents and kMaxSegments requests (the
+// worker thread only; index i has no launch in flight).
+void lshbloom_server::launch(uint32_t i) {
+    lshbloom *h = idx[i];
+    cudaStream_t s = sig_stream[i];
+    std::vector<Segment> segs;
+    std::vector<Request *> batch;
+    uint64_t D = 0, T = 0;
+    while (!sig_wait[i].empty() && segs.size() < kMaxSegments) {
+        Request *r = sig_wait[i].front();
+        if (!batch.empty() && D + r->D > kMaxLaunchDocs) break;
+        sig_wait[i].pop_front();
+        uint8_t *p = pool.base + r->pool_off;
+        cudaError_t e = cudaSuccess;
+        if (!r->in_off) {
+            r->d_off = (uint64_t *)p;
+            p += align256((r->D + 1) * 8);
+            e = cudaMemcpyAsync(r->d_off, r->h_off, (r->D + 1) * 8, cudaMemcpyHostToDevice, s);
+        }
+        if (e == cudaSuccess && !r->in_tok) {
+            r->d_tok = (uint32_t *)p;
+            p += align256(r->T * 4);
+            if (r->T)
+                e = cudaMemcpyAsync(r->d_tok, r->h_tok + r->tok0, r->T * 4, cudaMemcpyHostToDevice, s);
+        }
+        r->d_keys = (uint64_t *)p;
+        if (e != cudaSuccess) {
+            r->status = cuda_fail(e, "request copy-in");
+            continue;
+        }
+        Segment sg;
+        sg.offsets = r->in_off ? r->in_off : r->d_off;
+        sg.tokens = r->in_tok ? r->in_tok : r->d_tok;
+        sg.tok_base = r->in_tok ? 0 : r->tok0;
+        sg.doc0 = D;
+        sg.keys_out = r->d_keys;
+        segs.push_back(sg);
+        batch.push_back(r);
+        D += r->D;
+        T += r->T;
     }
-    if (!r->in_tok) {
-        r->d_tok = (uint32_t *)p;
-        p += align256(r->T * 4);
-        if (r->T && (e = cudaMemcpyAsync(r->d_tok, r->h_tok + r->tok0, r->T * 4,
-                                         cudaMemcpyHostToDevice, s)) != cudaSuccess)
-            return cuda_fail(e, "request tokens");
+    if (batch.empty()) return;
+    lshb_status st = launch_keys_segments(h, seg[i], segs.data(), (uint32_t)segs.size(), D, T, s);
+    cudaError_t e = cudaSuccess;
+    if (st == LSHB_OK && (e = cudaEventRecord(sig_event[i], s)) != cudaSuccess)
+        st = cuda_fail(e, "event");
+    if (st != LSHB_OK) {
+        cudaStreamSynchronize(s);
+        for (Request *r : batch) r->status = st;
+        return;
     }
-    r->d_keys = (uint64_t *)p;
-    p += align256(r->D * bands * 8);
-    r->d_flags = p;
-    lshbloom *h = idx[r->index];
-    const SigPass &ps = h->passes[0];
-    SigArgs a;
-    memset(&a, 0, sizeof a);
-    a.band_key = h->cfg.band_key;
-    a.offsets = r->in_off ? r->in_off : r->d_off;
-    a.tokens = r->in_tok ? r->in_tok : r->d_tok;
-    a.tok_base = r->in_tok ? 0 : r->tok0;
-    a.D = r->D;
-    a.ngram = h->ngram;
-    a.P = h->P;
-    a.bands = h->bands;
-    a.rows = h->rows;
-    a.p0 = 0;
-    a.npc = ps.npc;
-    a.c = ps.c;
-    a.keys_out = r->d_keys;
-    const int ngt = ngram_template(h->ngram);
-    if (ngt == 5) e = launch_sig_ng5(ps.ppl, a, s);
-    else if (ngt == 1) e = launch_sig_ng1(ps.ppl, a, s);
-    else e = launch_sig_ng0(ps.ppl, a, s);
-    if (e != cudaSuccess) return cuda_fail(e, "request signatures");
-    if ((e = cudaEventRecord(events[r->slot], s)) != cudaSuccess) return cuda_fail(e, "event");
-    return LSHB_OK;
+    sig_flight[i] = batch;
 }
 
 // Bloom stage of a group of requests of one index, in arrival order, as one
@@ -221,7 +241,7 @@ void lshbloom_server::loop() {
     std::unique_lock<std::mutex> lk(mu);
     for (;;) {
         // admission: FIFO head while a slot and enough memory are free
-        std::vector<Request *> admitted;
+        bool moved = false;
         while (!fifo.empty() && !free_slots.empty()) {
             Request *r = fifo.front();
             uint64_t off = 0;
@@ -232,48 +252,60 @@ void lshbloom_server::loop() {
             r->state = RState::Running;
             fifo.pop_front();
             running[r->index].push_back(r);
-            admitted.push_back(r);
+            sig_wait[r->index].push_back(r);
+            moved = true;
         }
         bool any_running = false;
         for (auto &q : running) any_running |= !q.empty();
         if (stop && fifo.empty() && !any_running) break;
         lk.unlock();
-        for (Request *r : admitted) {
-            lshb_status st = launch(r);
-            if (st != LSHB_OK) r->status = st;
+        // signature stages: a finished launch hands its requests to the Bloom
+        // stage; an idle index starts its waiting requests
+        for (uint32_t i = 0; i < idx.size(); ++i) {
+            if (!sig_flight[i].empty()) {
+                const cudaError_t q = cudaEventQuery(sig_event[i]);
+                if (q == cudaErrorNotReady) continue;
+                lshb_status st = LSHB_OK;
+                if (q != cudaSuccess) st = cuda_fail(q, "signature stage");
+                else if (segment_state_error(seg[i]) != 0)
+                    st = fail(LSHB_ERR_CUDA, "signature stage: device error word 0x%x",
+                              segment_state_error(seg[i]));
+                for (Request *r : sig_flight[i]) {
+                    if (st != LSHB_OK) r->status = st;
+                    r->keyed = true;
+                }
+                sig_flight[i].clear();
+                moved = true;
+            }
+            if (!sig_wait[i].empty()) {
+                launch(i);
+                moved = true;
+            }
         }
         // Bloom stage, per index in arrival order: the oldest requests whose
-        // signature stages are done, as one group
+        // band keys are ready, as one group
         std::vector<Request *> finished;
         for (size_t i = 0; i < running.size(); ++i) {
             for (;;) {
                 std::vector<Request *> group;
                 uint64_t docs = 0;
-                {
-                    std::lock_guard<std::mutex> g(mu);
-                    for (Request *r : running[i]) {
-                        if (!group.empty() && docs + r->D > kMaxGroupDocs) break;
-                        if (r->status == LSHB_OK) {
-                            const cudaError_t q = cudaEventQuery(events[r->slot]);
-                            if (q == cudaErrorNotReady) break;
-                            if (q != cudaSuccess) r->status = cuda_fail(q, "signature stage");
-                        }
-                        if (r->status != LSHB_OK) {
-                            if (group.empty()) group.push_back(r);  // fails alone
-                            break;
-                        }
-                        group.push_back(r);
-                        docs += r->D;
+                for (Request *r : running[i]) {
+                    if (!group.empty() && docs + r->D > kMaxGroupDocs) break;
+                    if (r->status != LSHB_OK) {
+                        // a failed request (its copy-in, its launch or its
+                        // signature stage failed: no launch holds it) finishes alone
+                        if (group.empty()) group.push_back(r);
+                        break;
                     }
+                    if (!r->keyed) break;
+                    group.push_back(r);
+                    docs += r->D;
                 }
                 if (group.empty()) break;
-                if (group.front()->status != LSHB_OK) {
-                    cudaStreamSynchronize(streams[group.front()->slot]);
-                } else {
+                if (group.front()->status == LSHB_OK) {
                     const lshb_status st = bloom(group);
                     for (Request *r : group) r->status = st;
                 }
-                std::lock_guard<std::mutex> g(mu);
                 for (size_t k = 0; k < group.size(); ++k) running[i].pop_front();
                 finished.insert(finished.end(), group.begin(), group.end());
             }
@@ -286,7 +318,7 @@ void lshbloom_server::loop() {
             free_slots.push_back(r->slot);
         }
         if (!finished.empty()) cv_done.notify_all();
-        if (admitted.empty() && finished.empty()) {
+        if (!moved && finished.empty()) {
             // nothing moved: wait for a submission or poll the GPU again soon
             cv_work.wait_for(lk, std::chrono::microseconds(50));
         }
@@ -324,14 +356,22 @@ extern "C" lshb_status lshbloom_server_create(lshbloom_t *const *indexes, uint32
         return fail(LSHB_ERR_OOM, "server budget of %llu bytes", (unsigned long long)mem_budget_bytes);
     }
     s->pool.init((uint8_t *)s->pool_mem, mem_budget_bytes & ~255ull);
-    s->streams.resize(max_inflight);
-    s->events.resize(max_inflight);
-    for (uint32_t i = 0; i < max_inflight; ++i) {
-        cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking);
-        cudaEventCreateWithFlags(&s->events[i], cudaEventDisableTiming);
-        s->free_slots.push_back((int)(max_inflight - 1 - i));
-    }
+    for (uint32_t i = 0; i < max_inflight; ++i) s->free_slots.push_back((int)(max_inflight - 1 - i));
     s->running.resize(n);
+    s->sig_wait.resize(n);
+    s->sig_flight.resize(n);
+    s->sig_stream.assign(n, nullptr);
+    s->sig_event.assign(n, nullptr);
+    s->seg.assign(n, nullptr);
+    for (uint32_t i = 0; i < n; ++i) {
+        cudaStreamCreateWithFlags(&s->sig_stream[i], cudaStreamNonBlocking);
+        cudaEventCreateWithFlags(&s->sig_event[i], cudaEventDisableTiming);
+        s->seg[i] = segment_state_create();
+        if (!s->seg[i]) {
+            lshbloom_server_destroy(s);
+            return fail(LSHB_ERR_OOM, "host allocation");
+        }
+    }
     s->worker = std::thread([s] { s->loop(); });
     *out = s;
     return LSHB_OK;
@@ -413,8 +453,11 @@ extern "C" void lshbloom_server_destroy(lshbloom_server_t *s) {
     if (s->worker.joinable()) s->worker.join();
     cudaSetDevice(s->device);
     for (auto &kv : s->reqs) delete kv.second;
-    for (auto st : s->streams) cudaStreamDestroy(st);
-    for (auto ev : s->events) cudaEventDestroy(ev);
+    for (auto st : s->sig_stream)
+        if (st) cudaStreamDestroy(st);
+    for (auto ev : s->sig_event)
+        if (ev) cudaEventDestroy(ev);
+    for (auto *st : s->seg) segment_state_destroy(st);
     if (s->pool_mem) cudaFree(s->pool_mem);
     delete s;
 }
