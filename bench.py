@@ -527,6 +527,7 @@ def _config_record(name, factory, n_docs, nexp, local, dev, stream, sync, steps,
              "resolve_sweeps_per_step": st["resolve_rounds"] / steps,
              "uncertain_docs_per_step": st["uncertain_docs"] / steps,
              "gpu_launches_per_step": st["launches"] / steps,
+             "chunk_docs": ix.stats()["chunk_docs"],
              "dups_per_step": int(flags.sum().item()), "clocks": clocks}
         rec[mode] = r
         ix.close()
@@ -777,8 +778,10 @@ def run_ours(args):
         configs["plain_10k"] = _config_record("plain_10k", "plain_10k", 10_000, 10_000, local, dev,
                                               stream, barrier_sync, 50, 5, cpu_cfg, 10_000,
                                               plain=True)
+        # 6 warm-up steps: the first five calls of >= 2^22 documents tune the
+        # chunk size (one with the largest candidate, then one per candidate)
         configs["pareto_8m"] = _config_record("pareto_8m", "pareto_batched", 8_000_000, 39_000_000,
-                                              local, dev, stream, barrier_sync, 5, 2, cpu_cfg,
+                                              local, dev, stream, barrier_sync, 5, 6, cpu_cfg,
                                               1_000_000, plain=True)
         torch.cuda.empty_cache()
         configs["billion_stream"] = _billion_record(local, dev, barrier_sync, args.billion_chunk,

@@ -141,7 +141,12 @@ typedef struct {
     const uint64_t *perm_b;   /* optional host array[P] of b_i in [0, 2^61-2] */
     uint32_t exec_mode;       /* lshb_exec_mode (default BATCHED) */
     int32_t device;           /* CUDA device ordinal, -1 = current */
-    uint64_t max_batch_docs;  /* docs per internal chunk, 0 = default (262144) */
+    uint64_t max_batch_docs;  /* docs per internal chunk, 0 = default: 262144 in the
+                                 plain form; in the batched form autotuned over calls
+                                 of at least 2^22 documents (the first four such
+                                 calls try 2^18, 2^19, 2^20 and 2^21 documents per
+                                 chunk, later ones keep the fastest per document),
+                                 2^20 until then */
     uint64_t max_batch_tokens;/* tokens per internal chunk, 0 = default (2^28 in the plain
                                  form; 2^31 in the batched form, where host inputs
                                  are staged through two device buffers of that size,
@@ -176,6 +181,8 @@ typedef struct {
     uint64_t h2d_bytes;       /* bytes those copies moved */
     double call_ms;           /* host wall-clock time spent inside dedup calls */
     uint64_t host_read_bytes; /* host token bytes the kernels read in place (no copy) */
+    uint64_t chunk_docs;      /* batched form: documents per internal chunk now in use
+                                 (max_batch_docs, or the autotuner's current choice) */
 } lshb_stats;
 
 /* Fill *cfg with defaults: P=121, b=11, r=11, n=5, n_expected=10000,

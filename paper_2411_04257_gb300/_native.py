@@ -39,7 +39,7 @@ class Stats(C.Structure):
         ("sig_ms", C.c_double), ("bloom_ms", C.c_double), ("sig_chunks", C.c_uint64),
         ("probe_ms", C.c_double), ("probe_sectors", C.c_uint64),
         ("h2d_ms", C.c_double), ("h2d_bytes", C.c_uint64), ("call_ms", C.c_double),
-        ("host_read_bytes", C.c_uint64),
+        ("host_read_bytes", C.c_uint64), ("chunk_docs", C.c_uint64),
     ]
 
 

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 
 #include "batched_kernels.cuh"
@@ -38,6 +39,7 @@ struct BatchedState {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // bracket the persistent kernel
     cudaEvent_t ev2 = nullptr;                  // end of the probe kernel (starts at ev1)
     cudaStream_t cap_stream = nullptr;          // private stream for graph capture
+    uint64_t graph_kernels = 0;                 // kernels one launch of the graph runs
 
     void drop_graph() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -205,7 +207,8 @@ static lshb_status ensure_state(lshbloom *h, uint64_t dcap, uint64_t tcap) {
         BCK(cudaEventCreate(&b->ev2));
         BCK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
     }
-    if (dcap > b->dcap) {
+    // the graph's grids and sketch follow the largest chunk of the call
+    if (dcap != b->dcap) {
         b->drop_graph();
         b->dcap = dcap;
     }
@@ -266,7 +269,9 @@ static lshb_status ensure_graph(lshbloom *h, cudaStream_t s) {
     lshb_status st = enqueue_front(h, b, make_args(h, b), true, cs, true);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &g);
-    // capture enqueues nothing: take back what the launch wrappers counted
+    // capture enqueues nothing: take back what the launch wrappers counted,
+    // and count it per graph launch instead
+    b->graph_kernels = launches_total() - counted;
     count_launch(counted - launches_total());
     if (st != LSHB_OK) {
         if (g) cudaGraphDestroy(g);
@@ -278,10 +283,56 @@ static lshb_status ensure_graph(lshbloom *h, cudaStream_t s) {
     return LSHB_OK;
 }
 
+// Chunk sizes the batched form's autotuner tries, in documents, on calls of at
+// least kChunkTuneMinDocs documents (smaller calls cannot tell them apart).
+constexpr uint64_t kChunkCandidates[4] = {1ull << 18, 1ull << 19, 1ull << 20, 1ull << 21};
+constexpr uint64_t kChunkTuneMinDocs = 1ull << 22;
+
+static lshb_status run_batched_chunks(lshbloom *h, const uint64_t *offsets,
+                                      const uint32_t *tokens, uint64_t D, uint8_t *flags,
+                                      const std::vector<uint64_t> &off, bool off_dev,
+                                      bool tok_dev, bool out_dev, cudaStream_t s,
+                                      uint64_t *keys_out, bool keys_dev);
+
+// Chunk size: max_batch_docs when set; otherwise, among calls of at least
+// kChunkTuneMinDocs documents, the first runs with the largest candidate (it
+// pays for allocations and the item-size tuning), the next four try each
+// candidate once, timing the whole call per document (chunking never changes
+// a result), and later calls keep the fastest.
 lshb_status run_batched(lshbloom *h, const uint64_t *offsets, const uint32_t *tokens, uint64_t D,
                         uint8_t *flags, const std::vector<uint64_t> &off, bool off_dev,
                         bool tok_dev, bool out_dev, cudaStream_t s, uint64_t *keys_out,
                         bool keys_dev) {
+    const bool tune = !h->cfg.max_batch_docs && !h->chunk_tuned && D >= kChunkTuneMinDocs;
+    const bool trial = tune && h->chunk_warm;
+    if (tune) h->max_docs_batched = kChunkCandidates[trial ? h->chunk_trial : 3];
+    if (tune && !trial) {
+        h->chunk_warm = true;
+        return run_batched_chunks(h, offsets, tokens, D, flags, off, off_dev, tok_dev, out_dev, s,
+                                  keys_out, keys_dev);
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    lshb_status st = run_batched_chunks(h, offsets, tokens, D, flags, off, off_dev, tok_dev,
+                                        out_dev, s, keys_out, keys_dev);
+    if (st != LSHB_OK || !trial) return st;
+    h->chunk_ms_per_doc[h->chunk_trial] =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() /
+        (double)D;
+    if (++h->chunk_trial == 4) {
+        uint32_t best = 0;
+        for (uint32_t c = 1; c < 4; ++c)
+            if (h->chunk_ms_per_doc[c] < h->chunk_ms_per_doc[best]) best = c;
+        h->max_docs_batched = kChunkCandidates[best];
+        h->chunk_tuned = true;
+    }
+    return LSHB_OK;
+}
+
+static lshb_status run_batched_chunks(lshbloom *h, const uint64_t *offsets,
+                                      const uint32_t *tokens, uint64_t D, uint8_t *flags,
+                                      const std::vector<uint64_t> &off, bool off_dev,
+                                      bool tok_dev, bool out_dev, cudaStream_t s,
+                                      uint64_t *keys_out, bool keys_dev) {
     if (off.size() != D + 1) return fail(LSHB_ERR_ARG, "offsets of %llu documents expected",
                                          (unsigned long long)D);
     // chunks: documents and (for staged or very large inputs) tokens bounded
@@ -351,7 +402,7 @@ lshb_status run_batched(lshbloom *h, const uint64_t *offsets, const uint32_t *to
         *b->dyn_host = dp;
         BCK(cudaEventRecord(h->ev_t[0], s));
         BCK(cudaGraphLaunch(b->exec, s));
-        count_launch(11);  // prepare, 3 scan, expand, persistent, probe, 4 classify kernels
+        count_launch(b->graph_kernels);  // prepare, scan, expand, persistent, probe, classify
         BCK(cudaEventRecord(h->ev_t[1], s));
         // Prefetch the next chunk's tokens only now, while this chunk computes:
         // a copy call that blocks the host then no longer idles the GPU.

@@ -38,9 +38,11 @@ __global__ void __launch_bounds__(kBloomThreads) k_probe(const __grid_constant__
     const uint64_t d = (uint64_t)blockIdx.x * kBloomThreads + threadIdx.x;
     const uint32_t j = blockIdx.y;
     if (d >= batch_docs(A)) return;
-    const uint64_t miss = probe_key<24>(A, j, A.keys[d * A.bands + j]);
-    A.miss[(uint64_t)j * A.mstride + d] = miss;
-    if (!miss) A.prehit[d] = 1;
+    uint64_t miss = probe_key<24>(A, j, A.keys[d * A.bands + j]);
+    uint64_t *mp = A.miss + (uint64_t)j * A.mstride + d;
+    if (!A.first_pass) miss |= *mp;
+    *mp = miss;
+    if (A.last_pass && !miss) A.prehit[d] = 1;
 }
 
 __global__ void __launch_bounds__(kBloomThreads) k_classify(const __grid_constant__ BloomArgs A) {
@@ -389,7 +391,8 @@ __global__ void __launch_bounds__(kBloomThreads) k_insert(const __grid_constant_
         const uint32_t u = __ffsll((long long)mm) - 1;
         mm &= mm - 1;
         const uint64_t q = ps.pos(u);
-        atomicOr(F + (q >> 5), 1u << (q & 31));
+        const uint64_t wi = q >> 5;
+        if (wi >= A.word_lo && wi < A.word_hi) atomicOr(F + wi, 1u << (q & 31));
     }
 }
 
@@ -445,8 +448,30 @@ cudaError_t launch_count_occupied(const uint64_t *slots, uint64_t n, unsigned lo
     return cudaGetLastError();
 }
 
+// Passes over the filters: one slice of at most kSliceBytes per pass when the
+// batch has enough probes per slice to reuse it (the exact key tables are not
+// sliced).
+static uint32_t filter_passes(const BloomArgs &a, uint64_t dcap) {
+    if (a.layout == 2 || dcap < (1ull << 15)) return 1;
+    const uint64_t p = (a.words_per_filter * 4 + kSliceBytes - 1) / kSliceBytes;
+    return (uint32_t)(p < 1 ? 1 : (p > 64 ? 1 : p));
+}
+
+static BloomArgs pass_args(BloomArgs a, uint32_t p, uint32_t np) {
+    const uint64_t per = (a.words_per_filter + np - 1) / np;
+    a.word_lo = per * p;
+    a.word_hi = p + 1 == np ? ~0ull : per * (p + 1);
+    a.first_pass = p == 0;
+    a.last_pass = p + 1 == np;
+    return a;
+}
+
 cudaError_t launch_probe(const BloomArgs &a, uint64_t dcap, cudaStream_t s) {
-    k_probe<<<band_grid(dcap, a.bands), kBloomThreads, 0, s>>>(a); count_launch();
+    const uint32_t np = filter_passes(a, dcap);
+    for (uint32_t p = 0; p < np; ++p) {
+        k_probe<<<band_grid(dcap, a.bands), kBloomThreads, 0, s>>>(pass_args(a, p, np));
+        count_launch();
+    }
     return cudaGetLastError();
 }
 
@@ -506,7 +531,11 @@ cudaError_t launch_finalize_insert(const BloomArgs &a, const uint32_t *ulist, ui
                                    uint8_t *insd, unsigned long long *dup_count, cudaStream_t s) {
     k_finalize<<<grid_for(a.D, 256), 256, 0, s>>>(a, ulist, nu, t, insert_all, flags, insd,
                                                    dup_count); count_launch();
-    k_insert<<<band_grid(a.D, a.bands), kBloomThreads, 0, s>>>(a, insd); count_launch();
+    const uint32_t np = filter_passes(a, a.D);
+    for (uint32_t p = 0; p < np; ++p) {
+        k_insert<<<band_grid(a.D, a.bands), kBloomThreads, 0, s>>>(pass_args(a, p, np), insd);
+        count_launch();
+    }
     return cudaGetLastError();
 }
 

@@ -32,7 +32,18 @@ struct BloomArgs {
     uint64_t *cand;             // D: candidate bands
     uint8_t *prehit;            // D
     uint32_t *error;            // device error word
+    // Probe and insert passes over one slice of each band's filter: only
+    // positions in filter words [word_lo, word_hi) are handled; the first
+    // pass writes the miss masks, later ones OR into them, the last one
+    // records the documents with a band that missed nothing.
+    uint64_t word_lo, word_hi;
+    uint32_t first_pass, last_pass;
 };
+
+// Bytes of a band's filter one probe or insert pass covers: with the band's
+// sketch and the streaming keys and masks it leaves most of the 129 MB L2 to
+// the slice, so repeated probes of a sector hit L2 instead of DRAM.
+constexpr uint64_t kSliceBytes = 32ull << 20;
 
 // Resolution table of the candidate bits of the uncertain documents: one
 // open-addressing segment per band (keys are positions inside that band's
@@ -129,12 +140,17 @@ __device__ __forceinline__ uint64_t probe_key(const BloomArgs &A, uint32_t j, ui
     uint64_t miss = 0;
     if (A.k <= (uint32_t)KMAX) {
         uint32_t w[KMAX];
+        uint32_t in = 0;  // probes whose word lies in this pass's slice
+#pragma unroll
+        for (int u = 0; u < KMAX; ++u) {
+            const uint64_t wi = ps.pos(u) >> 5;
+            const bool here = u < (int)A.k && wi >= A.word_lo && wi < A.word_hi;
+            in |= (uint32_t)here << u;
+            w[u] = here ? __ldg(F + wi) : 0xffffffffu;
+        }
 #pragma unroll
         for (int u = 0; u < KMAX; ++u)
-            w[u] = (u < (int)A.k) ? __ldg(F + (ps.pos(u) >> 5)) : 0xffffffffu;
-#pragma unroll
-        for (int u = 0; u < KMAX; ++u)
-            if (!((w[u] >> (ps.pos(u) & 31)) & 1u)) miss |= 1ull << u;
+            if (((in >> u) & 1u) && !((w[u] >> (ps.pos(u) & 31)) & 1u)) miss |= 1ull << u;
         uint32_t *S = A.sketch + (uint64_t)j * (A.sketch_cells >> 4);
 #pragma unroll
         for (int u = 0; u < KMAX; ++u) {
@@ -156,12 +172,18 @@ __device__ __forceinline__ uint64_t probe_key(const BloomArgs &A, uint32_t j, ui
     } else {
         for (uint32_t u0 = 0; u0 < A.k; u0 += 8) {
             uint32_t w[8];
+            uint32_t in = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const uint64_t wi = ps.pos(u0 + i) >> 5;
+                const bool here = u0 + i < A.k && wi >= A.word_lo && wi < A.word_hi;
+                in |= (uint32_t)here << i;
+                w[i] = here ? __ldg(F + wi) : 0xffffffffu;
+            }
 #pragma unroll
             for (int i = 0; i < 8; ++i)
-                w[i] = (u0 + i < A.k) ? __ldg(F + (ps.pos(u0 + i) >> 5)) : 0xffffffffu;
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-                if (!((w[i] >> (ps.pos(u0 + i) & 31)) & 1u)) miss |= 1ull << (u0 + i);
+                if (((in >> i) & 1u) && !((w[i] >> (ps.pos(u0 + i) & 31)) & 1u))
+                    miss |= 1ull << (u0 + i);
         }
     }
     uint64_t mm = miss;

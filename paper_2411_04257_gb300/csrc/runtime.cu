@@ -657,6 +657,9 @@ BloomArgs lshb::bloom_args(lshbloom *h, uint64_t D, uint64_t dcap) {
     b.cand = (uint64_t *)h->buf(B_CAND).ptr;
     b.prehit = (uint8_t *)h->buf(B_PREHIT).ptr;
     b.error = h->counters + C_ERROR;
+    b.word_lo = 0;
+    b.word_hi = ~0ull;
+    b.first_pass = b.last_pass = 1;
     return b;
 }
 
@@ -1069,6 +1072,7 @@ extern "C" lshb_status lshbloom_stats(lshbloom_t *h, lshb_stats *out) {
     out->h2d_bytes = h->h2d_bytes;
     out->call_ms = h->t_call_ms;
     out->host_read_bytes = h->host_read_bytes;
+    out->chunk_docs = h->max_docs_batched;
     unsigned long long *cnt = (unsigned long long *)(h->counters + C_POPCOUNT);
     const bool exact = h->layout == LSHB_EXACT_KEYS;
     for (uint32_t j = 0; j < h->bands; ++j) {

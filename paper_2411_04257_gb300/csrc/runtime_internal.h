@@ -85,6 +85,11 @@ struct lshbloom {
     lshb::DevBuf bufs[lshb::B_NBUF];
     uint64_t max_docs = 0, max_tokens = 0;
     uint64_t max_docs_batched = 0, max_tokens_batched = 0;
+    // batched-form chunk autotuner (max_batch_docs = 0): candidate being
+    // tried, wall time per document of each tried candidate, and the choice
+    uint32_t chunk_trial = 0;
+    double chunk_ms_per_doc[4] = {0, 0, 0, 0};
+    bool chunk_warm = false, chunk_tuned = false;
     uint32_t item_shingles = 0;
     lshb::BatchedState *batched = nullptr;
     uint64_t docs_seen = 0, dups_seen = 0, resolve_rounds = 0, uncertain_docs = 0;

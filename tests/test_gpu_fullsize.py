@@ -110,3 +110,30 @@ def test_billion_stream_prefix_three_calls(lshb, oracle):
     ix, flags, _ = _check_exact(lshb, oracle, spec, 1_000_000_000, calls=3)
     assert flags.sum() > 20_000
     ix.close()
+
+
+def test_chunk_autotuner_keeps_the_results(lshb):
+    """Calls of at least 2^22 documents tune the batched form's chunk size: the
+    first runs with 2^21 documents per chunk, the next four try 2^18 .. 2^21,
+    later ones keep the fastest.  Chunking never changes a result: with the
+    index cleared before each call, every call gives the same flags."""
+    from synth import corpus
+    from synth import gpu as sgpu
+    n = 1 << 22
+    spec = corpus.pareto_batched(n_docs=n)
+    off, tok = sgpu.DeviceCorpus(spec).generate(0, n)
+    ix = lshb.LSHBloom(P, BANDS, ROWS, n_expected=39_000_000, fp_rate=1e-5)
+    first, chunks = None, []
+    for _ in range(6):
+        ix.reset()
+        f = ix.dedup(off, tok).cpu().numpy()
+        chunks.append(ix.stats()["chunk_docs"])
+        if first is None:
+            first = f
+        else:
+            assert np.array_equal(f, first)
+    cands = [1 << 18, 1 << 19, 1 << 20, 1 << 21]
+    assert chunks[:4] == [1 << 21, 1 << 18, 1 << 19, 1 << 20]
+    assert chunks[4] in cands and chunks[5] == chunks[4]
+    assert first.sum() > 100_000
+    ix.close()
