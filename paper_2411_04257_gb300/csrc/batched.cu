@@ -140,6 +140,7 @@ static BatchArgs make_args(lshbloom *h, BatchedState *b) {
     a.sig_partial = (uint32_t *)b->sig_partial.ptr;
     a.queue = (unsigned long long *)(h->counters + C_QUEUE);
     a.keys = (uint64_t *)h->buf(B_KEYS).ptr;
+    a.key_rows = b->dcap;
     a.cand = (uint64_t *)h->buf(B_CAND).ptr;
     a.prehit = (uint8_t *)h->buf(B_PREHIT).ptr;
     a.error = h->counters + C_ERROR;
@@ -172,6 +173,8 @@ static lshb_status enqueue_front(lshbloom *h, BatchedState *b, BatchArgs a, bool
     const uint64_t dcap = b->dcap;
     BloomArgs A = bloom_args(h, dcap, dcap);
     A.D_dev = &b->dyn->D;
+    A.key_sd = 1;  // the persistent kernel writes the keys band-major
+    A.key_sj = dcap;
     BCK(cudaMemcpyAsync(b->dyn, b->dyn_host, sizeof(DynParams), cudaMemcpyHostToDevice, s));
     BCK(cudaMemsetAsync(h->counters, 0, kChunkCounterBytes, s));
     if (with_bloom)
@@ -361,6 +364,9 @@ static lshb_status run_batched_chunks(lshbloom *h, const uint64_t *offsets,
     BatchedState *b = h->batched;
     DevBuf &outbuf = h->buf(B_OUTSTAGE);
     if (!out_dev && (st = outbuf.reserve(b->dcap)) != LSHB_OK) return st;
+    DevBuf &keystage = h->buf(B_KEYSTAGE);  // row-major keys on their way to host keys_out
+    if (keys_out && !keys_dev && (st = keystage.reserve(b->dcap * h->bands * 8)) != LSHB_OK)
+        return st;
     uint64_t *d_off_stage = (uint64_t *)h->buf(B_OFFSTAGE).ptr;
 
     auto issue_copy = [&](size_t ci) -> lshb_status {
@@ -414,10 +420,20 @@ static lshb_status run_batched_chunks(lshbloom *h, const uint64_t *offsets,
         BCK(cudaEventElapsedTime(&ms_probe, b->ev1, b->ev2));
         h->t_probe_ms += ms_probe;
         h->probe_sectors += Dn * h->bands * probe_sectors_per_key(h);
-        if (keys_out)
-            BCK(cudaMemcpyAsync(keys_out + lo * h->bands, h->buf(B_KEYS).ptr, Dn * h->bands * 8,
-                                keys_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+        if (keys_out) {
+            // the keys, band-major in B_KEYS, leave row-major
+            uint64_t *dst = keys_dev ? keys_out + lo * h->bands : (uint64_t *)keystage.ptr;
+            const uint64_t n = Dn * h->bands;
+            k_keys_row_major<<<(unsigned)std::min<uint64_t>((n + 255) / 256, 8192), 256, 0, s>>>(
+                (const uint64_t *)h->buf(B_KEYS).ptr, b->dcap, Dn, h->bands, dst);
+            count_launch();
+            BCK(cudaGetLastError());
+            if (!keys_dev)
+                BCK(cudaMemcpyAsync(keys_out + lo * h->bands, dst, n * 8, cudaMemcpyDeviceToHost, s));
+        }
         BloomArgs A = bloom_args(h, Dn, b->dcap);
+        A.key_sd = 1;
+        A.key_sj = b->dcap;
         uint8_t *fl = out_dev ? flags + lo : (uint8_t *)outbuf.ptr;
         if ((st = resolve_and_insert(h, A, fl, s)) != LSHB_OK) return st;
         BCK(cudaEventRecord(h->ev_t[2], s));

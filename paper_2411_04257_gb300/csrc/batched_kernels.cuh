@@ -25,23 +25,28 @@ struct DynParams {
 };
 
 // Where document d of a launch lives: its offsets (indexed by `local`), its
-// token base and the row of its band keys.
+// token base and its band keys (band j at keys[j * key_sj]).
 struct DocRef {
     const uint64_t *offsets;
     const uint32_t *tokens;
     uint64_t tok_base, local;
     uint64_t *keys;
+    uint64_t key_sj;
 };
 
-__device__ __forceinline__ DocRef doc_ref(const DynParams &dp, uint64_t *keys, uint32_t bands,
-                                          uint64_t d) {
+// A single-batch launch writes the keys band-major (band j of document d at
+// keys[j * key_rows + d], so the band-by-band Bloom kernels read them
+// coalesced); a multi-batch launch writes each batch's keys row-major.
+__device__ __forceinline__ DocRef doc_ref(const DynParams &dp, uint64_t *keys, uint64_t key_rows,
+                                          uint32_t bands, uint64_t d) {
     DocRef r;
     if (dp.nseg == 0) {
         r.offsets = dp.offsets;
         r.tokens = dp.tokens;
         r.tok_base = dp.tok_base;
         r.local = d;
-        r.keys = keys + d * bands;
+        r.keys = keys + d;
+        r.key_sj = key_rows;
         return r;
     }
     uint32_t lo = 0, hi = dp.nseg - 1;  // last segment with doc0 <= d
@@ -55,6 +60,7 @@ __device__ __forceinline__ DocRef doc_ref(const DynParams &dp, uint64_t *keys, u
     r.tok_base = sg.tok_base;
     r.local = d - sg.doc0;
     r.keys = sg.keys_out + r.local * bands;
+    r.key_sj = 1;
     return r;
 }
 
@@ -69,7 +75,8 @@ struct BatchArgs {
     uint32_t *pending;         // D: items of the document not finished yet
     uint32_t *sig_partial;     // D x P: merged minima of split documents
     unsigned long long *queue;
-    uint64_t *keys;            // D x bands (single-batch launches)
+    uint64_t *keys;            // single-batch launches: bands x key_rows, band-major
+    uint64_t key_rows;         // row length of keys (the chunk capacity)
     uint64_t *cand;            // D: cleared for the Bloom stage (nullptr: left alone)
     uint8_t *prehit;           // D: cleared for the Bloom stage (nullptr: left alone)
     uint32_t *error;
@@ -87,7 +94,7 @@ __global__ void k_batch_prepare(const __grid_constant__ BatchArgs A) {
     const DynParams dp = *A.dyn;
     for (uint64_t d = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; d < dp.D;
          d += (uint64_t)gridDim.x * blockDim.x) {
-        const DocRef r = doc_ref(dp, A.keys, A.bands, d);
+        const DocRef r = doc_ref(dp, A.keys, A.key_rows, A.bands, d);
         const uint64_t L = r.offsets[r.local + 1] - r.offsets[r.local];
         const uint64_t it = items_of(L, A.ngram, A.item_shingles);
         A.item_count[d] = (uint32_t)it;
@@ -98,6 +105,19 @@ __global__ void k_batch_prepare(const __grid_constant__ BatchArgs A) {
             uint32_t *row = A.sig_partial + d * A.P;
             for (uint32_t p = 0; p < A.P; ++p) row[p] = 0xffffffffu;
         }
+    }
+}
+
+// Band-major keys (bands x rows) of the first D documents to row-major
+// (D x bands), for callers that asked for the keys.
+__global__ void k_keys_row_major(const uint64_t *__restrict__ src, uint64_t rows, uint64_t D,
+                                 uint32_t bands, uint64_t *__restrict__ dst) {
+    const uint64_t n = D * bands;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t d = i / bands;
+        const uint32_t j = (uint32_t)(i - d * bands);
+        dst[i] = src[(uint64_t)j * rows + d];
     }
 }
 
@@ -203,7 +223,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batched(const __grid_constant
             if (lane == 0) atomicOr(A.error, kErrQueue);
             continue;
         }
-        const DocRef r = doc_ref(dp, A.keys, A.bands, d);
+        const DocRef r = doc_ref(dp, A.keys, A.key_rows, A.bands, d);
         const uint64_t o0 = r.offsets[r.local];
         const uint64_t L = r.offsets[r.local + 1] - o0;
         const uint32_t *tk = r.tokens + (o0 - r.tok_base);
@@ -234,7 +254,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batched(const __grid_constant
         for (int t = 0; t < PPL; ++t) sigbuf[lane + 32 * t] = mn[t];
         __syncwarp();
         for (uint32_t j = lane; j < A.bands; j += 32)
-            r.keys[j] = band_key_of(sigbuf + j * A.rows, A.rows, j, A.band_key);
+            r.keys[j * r.key_sj] = band_key_of(sigbuf + j * A.rows, A.rows, j, A.band_key);
         __syncwarp();
     }
 }

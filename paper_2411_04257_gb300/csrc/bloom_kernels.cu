@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kBloomThreads) k_probe(const __grid_constant__
     const uint64_t d = (uint64_t)blockIdx.x * kBloomThreads + threadIdx.x;
     const uint32_t j = blockIdx.y;
     if (d >= batch_docs(A)) return;
-    uint64_t miss = probe_key<24>(A, j, A.keys[d * A.bands + j]);
+    uint64_t miss = probe_key<24>(A, j, band_key(A, d, j));
     uint64_t *mp = A.miss + (uint64_t)j * A.mstride + d;
     if (!A.first_pass) miss |= *mp;
     *mp = miss;
@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kBloomThreads) k_classify(const __grid_constan
     if (d >= batch_docs(A)) return;
     uint64_t mm = A.miss[(uint64_t)j * A.mstride + d];
     if (!mm) return;
-    const ProbeSeq ps(A.keys[d * A.bands + j], j, A.m_bits, A.layout);
+    const ProbeSeq ps(band_key(A, d, j), j, A.m_bits, A.layout);
     bool all = true;
     while (mm && all) {
         const uint32_t u = __ffsll((long long)mm) - 1;
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kBloomThreads) k_rk_insert(const __grid_consta
     if (ui >= nu) return;
     const uint32_t d = ulist[ui];
     if (!((A.cand[d] >> j) & 1ull)) return;
-    const ProbeSeq ps(A.keys[(uint64_t)d * A.bands + j], j, A.m_bits, A.layout);
+    const ProbeSeq ps(band_key(A, d, j), j, A.m_bits, A.layout);
     uint64_t mm = A.miss[(uint64_t)j * A.mstride + d];
     while (mm) {
         const uint32_t u = __ffsll((long long)mm) - 1;
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kBloomThreads) k_fixed_setters(
     if (!insert_all && A.status[d] != 0) return;
     uint64_t mm = A.miss[(uint64_t)j * A.mstride + d];
     if (!mm) return;
-    const ProbeSeq ps(A.keys[d * A.bands + j], j, A.m_bits, A.layout);
+    const ProbeSeq ps(band_key(A, d, j), j, A.m_bits, A.layout);
     while (mm) {
         const uint32_t u = __ffsll((long long)mm) - 1;
         mm &= mm - 1;
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(kBloomThreads) k_cache_slots(const __grid_cons
     if (ui >= nu) return;
     const uint32_t d = ulist[ui];
     const uint64_t miss = A.miss[(uint64_t)j * A.mstride + d];
-    const ProbeSeq ps(A.keys[(uint64_t)d * A.bands + j], j, A.m_bits, A.layout);
+    const ProbeSeq ps(band_key(A, d, j), j, A.m_bits, A.layout);
     uint32_t *out = T.slots + ((uint64_t)ui * A.bands + j) * A.k;
     for (uint32_t u = 0; u < A.k; ++u)
         out[u] = ((miss >> u) & 1ull) ? ht_find(T, j, ps.pos(u)) : kNone;
@@ -382,11 +382,11 @@ __global__ void __launch_bounds__(kBloomThreads) k_insert(const __grid_constant_
     if (!mm) return;
     uint32_t *F = A.filters + (uint64_t)j * A.words_per_filter;
     if (A.layout == 2) {
-        if (!exact_insert(reinterpret_cast<uint64_t *>(F), A.exact_cap, A.keys[d * A.bands + j]))
+        if (!exact_insert(reinterpret_cast<uint64_t *>(F), A.exact_cap, band_key(A, d, j)))
             atomicOr(A.error, kErrTableFull);
         return;
     }
-    const ProbeSeq ps(A.keys[d * A.bands + j], j, A.m_bits, A.layout);
+    const ProbeSeq ps(band_key(A, d, j), j, A.m_bits, A.layout);
     while (mm) {
         const uint32_t u = __ffsll((long long)mm) - 1;
         mm &= mm - 1;

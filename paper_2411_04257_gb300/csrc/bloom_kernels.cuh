@@ -23,7 +23,8 @@ struct BloomArgs {
     uint64_t m_bits, words_per_filter;
     uint64_t exact_cap;         // exact layout: slots of each band's key table (power of two)
     uint32_t *filters;          // bands x words_per_filter
-    const uint64_t *keys;       // D x bands, row-major
+    const uint64_t *keys;       // band j of document d at keys[d * key_sd + j * key_sj]
+    uint64_t key_sd, key_sj;    // row-major (bands, 1) or band-major (1, row length)
     uint64_t *miss;             // bands x mstride, band-major: bit u = probe u found a clear bit
     uint64_t mstride;           // row stride of miss (>= D)
     uint32_t *sketch;           // bands x (sketch_cells / 16) words of 2-bit cells
@@ -67,6 +68,10 @@ constexpr uint32_t kNone = 0xffffffffu;
 
 __device__ __forceinline__ uint64_t batch_docs(const BloomArgs &A) {
     return A.D_dev ? *A.D_dev : A.D;
+}
+
+__device__ __forceinline__ uint64_t band_key(const BloomArgs &A, uint64_t d, uint32_t j) {
+    return A.keys[d * A.key_sd + (uint64_t)j * A.key_sj];
 }
 
 // Sketch cell of position `pos` in its band's sketch: multiplicative hash,

@@ -649,6 +649,8 @@ BloomArgs lshb::bloom_args(lshbloom *h, uint64_t D, uint64_t dcap) {
     b.exact_cap = h->exact_cap;
     b.filters = h->filters;
     b.keys = (const uint64_t *)h->buf(B_KEYS).ptr;
+    b.key_sd = h->bands;  // row-major; the batched form switches to band-major
+    b.key_sj = 1;
     b.miss = (uint64_t *)h->buf(B_MISS).ptr;
     b.mstride = dcap;
     b.sketch = (uint32_t *)h->buf(B_SKETCH).ptr;

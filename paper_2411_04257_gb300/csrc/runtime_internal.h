@@ -25,7 +25,7 @@ struct DevBuf {
 enum BufId {
     B_KEYS, B_MISS, B_CAND, B_STATUS, B_PREHIT, B_FLAGS, B_INSD, B_ULIST, B_BLOCKCNT, B_OFFSTAGE,
     B_SIG, B_HASHES, B_SKETCH, B_HT_KEYS, B_HT_FIXED, B_HT_FIRST, B_HT_SLOTS,
-    B_HT_INS, B_HT_UDUP, B_HASHOUT, B_OUTSTAGE, B_ITEMS, B_PENDING, B_NBUF
+    B_HT_INS, B_HT_UDUP, B_HASHOUT, B_OUTSTAGE, B_KEYSTAGE, B_NBUF
 };
 
 // Slots of the device counter block (uint32 units; kCounterBytes in all).
