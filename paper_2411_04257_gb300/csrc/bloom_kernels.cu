@@ -448,9 +448,9 @@ cudaError_t launch_count_occupied(const uint64_t *slots, uint64_t n, unsigned lo
     return cudaGetLastError();
 }
 
-// Passes over the filters: one slice of at most kSliceBytes per pass when the
-// batch has enough probes per slice to reuse it (the exact key tables are not
-// sliced).
+// Insert passes over the filters: one slice of at most kSliceBytes per pass
+// when the batch has enough bits to set per slice to reuse it (the exact key
+// tables are not sliced).
 static uint32_t filter_passes(const BloomArgs &a, uint64_t dcap) {
     if (a.layout == 2 || dcap < (1ull << 15)) return 1;
     const uint64_t p = (a.words_per_filter * 4 + kSliceBytes - 1) / kSliceBytes;
@@ -467,11 +467,8 @@ static BloomArgs pass_args(BloomArgs a, uint32_t p, uint32_t np) {
 }
 
 cudaError_t launch_probe(const BloomArgs &a, uint64_t dcap, cudaStream_t s) {
-    const uint32_t np = filter_passes(a, dcap);
-    for (uint32_t p = 0; p < np; ++p) {
-        k_probe<<<band_grid(dcap, a.bands), kBloomThreads, 0, s>>>(pass_args(a, p, np));
-        count_launch();
-    }
+    k_probe<<<band_grid(dcap, a.bands), kBloomThreads, 0, s>>>(pass_args(a, 0, 1));
+    count_launch();
     return cudaGetLastError();
 }
 
