@@ -53,7 +53,7 @@ struct Request {
     uint32_t *d_tok = nullptr;
     uint64_t *d_keys = nullptr;
     int slot = -1;
-    bool keyed = false;  // band keys are in d_keys
+    bool keyed = false;  // the signature stage is over (band keys in d_keys, or a failure)
     RState state = RState::Pending;
     lshb_status status = LSHB_OK;
     Clock::time_point t_submit, t_done;
@@ -125,13 +125,18 @@ struct lshbloom_server {
     std::vector<std::vector<Request *>> sig_flight;
     std::unordered_map<uint64_t, Request *> reqs;
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
-    std::thread worker;
+    // cv_work: submissions and freed memory (the signature thread);
+    // cv_bloom: requests whose signature stage ended (the Bloom threads);
+    // cv_done: finished requests (callers of lshbloom_server_wait)
+    std::condition_variable cv_work, cv_bloom, cv_done;
+    std::thread worker;                    // admission and signature launches
+    std::vector<std::thread> bloom_workers;  // one per index: its Bloom stages
     bool stop = false;
     uint64_t next_ticket = 1;
 
     void loop();
-    void launch(uint32_t i);
+    void bloom_loop(uint32_t i);
+    std::vector<Request *> launch(uint32_t i);
     lshb_status bloom(const std::vector<Request *> &group);
 };
 
@@ -151,8 +156,11 @@ static uint64_t request_bytes(uint64_t D, uint64_t T, uint32_t bands, bool copy_
 
 // One signature launch for index i: the oldest admitted requests not yet
 // started, up to kMaxLaunchDocs documents and kMaxSegments requests (the
-// worker thread only; index i has no launch in flight).
-void lshbloom_server::launch(uint32_t i) {
+// signature thread only; index i has no launch in flight).  Returns the
+// requests that failed before or at the launch, their status set, for the
+// caller to hand on under the lock.
+std::vector<Request *> lshbloom_server::launch(uint32_t i) {
+    std::vector<Request *> failed;
     lshbloom *h = idx[i];
     cudaStream_t s = sig_stream[i];
     std::vector<Segment> segs;
@@ -178,6 +186,7 @@ void lshbloom_server::launch(uint32_t i) {
         r->d_keys = (uint64_t *)p;
         if (e != cudaSuccess) {
             r->status = cuda_fail(e, "request copy-in");
+            failed.push_back(r);
             continue;
         }
         Segment sg;
@@ -191,7 +200,7 @@ void lshbloom_server::launch(uint32_t i) {
         D += r->D;
         T += r->T;
     }
-    if (batch.empty()) return;
+    if (batch.empty()) return failed;
     lshb_status st = launch_keys_segments(h, seg[i], segs.data(), (uint32_t)segs.size(), D, T, s);
     cudaError_t e = cudaSuccess;
     if (st == LSHB_OK && (e = cudaEventRecord(sig_event[i], s)) != cudaSuccess)
@@ -199,9 +208,11 @@ void lshbloom_server::launch(uint32_t i) {
     if (st != LSHB_OK) {
         cudaStreamSynchronize(s);
         for (Request *r : batch) r->status = st;
-        return;
+        failed.insert(failed.end(), batch.begin(), batch.end());
+        return failed;
     }
     sig_flight[i] = batch;
+    return failed;
 }
 
 // Bloom stage of a group of requests of one index, in arrival order, as one
@@ -236,6 +247,7 @@ lshb_status lshbloom_server::bloom(const std::vector<Request *> &group) {
     return LSHB_OK;
 }
 
+// The signature thread: admission, signature launches, their completion.
 void lshbloom_server::loop() {
     cudaSetDevice(device);
     std::unique_lock<std::mutex> lk(mu);
@@ -259,8 +271,10 @@ void lshbloom_server::loop() {
         for (auto &q : running) any_running |= !q.empty();
         if (stop && fifo.empty() && !any_running) break;
         lk.unlock();
-        // signature stages: a finished launch hands its requests to the Bloom
-        // stage; an idle index starts its waiting requests
+        // a finished launch hands its requests to the Bloom threads; an idle
+        // index starts its waiting requests
+        std::vector<Request *> ended;
+        std::vector<lshb_status> ended_status;
         for (uint32_t i = 0; i < idx.size(); ++i) {
             if (!sig_flight[i].empty()) {
                 const cudaError_t q = cudaEventQuery(sig_event[i]);
@@ -271,57 +285,72 @@ void lshbloom_server::loop() {
                     st = fail(LSHB_ERR_CUDA, "signature stage: device error word 0x%x",
                               segment_state_error(seg[i]));
                 for (Request *r : sig_flight[i]) {
-                    if (st != LSHB_OK) r->status = st;
-                    r->keyed = true;
+                    ended.push_back(r);
+                    ended_status.push_back(st);
                 }
                 sig_flight[i].clear();
                 moved = true;
             }
             if (!sig_wait[i].empty()) {
-                launch(i);
+                for (Request *r : launch(i)) {
+                    ended.push_back(r);
+                    ended_status.push_back(r->status);
+                }
                 moved = true;
             }
         }
-        // Bloom stage, per index in arrival order: the oldest requests whose
-        // band keys are ready, as one group
-        std::vector<Request *> finished;
-        for (size_t i = 0; i < running.size(); ++i) {
-            for (;;) {
-                std::vector<Request *> group;
-                uint64_t docs = 0;
-                for (Request *r : running[i]) {
-                    if (!group.empty() && docs + r->D > kMaxGroupDocs) break;
-                    if (r->status != LSHB_OK) {
-                        // a failed request (its copy-in, its launch or its
-                        // signature stage failed: no launch holds it) finishes alone
-                        if (group.empty()) group.push_back(r);
-                        break;
-                    }
-                    if (!r->keyed) break;
-                    group.push_back(r);
-                    docs += r->D;
-                }
-                if (group.empty()) break;
-                if (group.front()->status == LSHB_OK) {
-                    const lshb_status st = bloom(group);
-                    for (Request *r : group) r->status = st;
-                }
-                for (size_t k = 0; k < group.size(); ++k) running[i].pop_front();
-                finished.insert(finished.end(), group.begin(), group.end());
+        lk.lock();
+        for (size_t k = 0; k < ended.size(); ++k) {
+            if (ended_status[k] != LSHB_OK) ended[k]->status = ended_status[k];
+            ended[k]->keyed = true;
+        }
+        if (!ended.empty()) cv_bloom.notify_all();
+        if (!moved) {
+            // nothing moved: wait for a submission or freed memory, or poll
+            // the GPU again soon
+            cv_work.wait_for(lk, std::chrono::microseconds(50));
+        }
+    }
+}
+
+// The Bloom thread of index i: the oldest requests of the index whose
+// signature stage has ended, as one group, in arrival order.
+void lshbloom_server::bloom_loop(uint32_t i) {
+    cudaSetDevice(device);
+    std::unique_lock<std::mutex> lk(mu);
+    for (;;) {
+        cv_bloom.wait(lk, [&] {
+            return (!running[i].empty() && running[i].front()->keyed) ||
+                   (stop && fifo.empty() && running[i].empty());
+        });
+        if (running[i].empty()) break;  // stopping, nothing left for this index
+        std::vector<Request *> group;
+        uint64_t docs = 0;
+        for (Request *r : running[i]) {
+            if (!r->keyed) break;
+            if (r->status != LSHB_OK) {
+                if (group.empty()) group.push_back(r);  // a failed request finishes alone
+                break;
             }
+            if (!group.empty() && docs + r->D > kMaxGroupDocs) break;
+            group.push_back(r);
+            docs += r->D;
+        }
+        lk.unlock();
+        if (group.front()->status == LSHB_OK) {
+            const lshb_status st = bloom(group);
+            for (Request *r : group) r->status = st;
         }
         lk.lock();
-        for (Request *r : finished) {
+        for (size_t k = 0; k < group.size(); ++k) running[i].pop_front();
+        for (Request *r : group) {
             r->t_done = Clock::now();
             r->state = RState::Done;
             pool.release(r->pool_off, r->bytes);
             free_slots.push_back(r->slot);
         }
-        if (!finished.empty()) cv_done.notify_all();
-        if (!moved && finished.empty()) {
-            // nothing moved: wait for a submission or poll the GPU again soon
-            cv_work.wait_for(lk, std::chrono::microseconds(50));
-        }
+        cv_done.notify_all();
+        cv_work.notify_one();
     }
 }
 
@@ -373,6 +402,7 @@ extern "C" lshb_status lshbloom_server_create(lshbloom_t *const *indexes, uint32
         }
     }
     s->worker = std::thread([s] { s->loop(); });
+    for (uint32_t i = 0; i < n; ++i) s->bloom_workers.emplace_back([s, i] { s->bloom_loop(i); });
     *out = s;
     return LSHB_OK;
 }
@@ -450,7 +480,16 @@ extern "C" void lshbloom_server_destroy(lshbloom_server_t *s) {
         s->stop = true;
     }
     s->cv_work.notify_all();
+    s->cv_bloom.notify_all();
     if (s->worker.joinable()) s->worker.join();
+    {
+        // the signature thread is gone: every admitted request has ended its
+        // signature stage; wake the Bloom threads to drain and stop
+        std::lock_guard<std::mutex> g(s->mu);
+    }
+    s->cv_bloom.notify_all();
+    for (auto &t : s->bloom_workers)
+        if (t.joinable()) t.join();
     cudaSetDevice(s->device);
     for (auto &kv : s->reqs) delete kv.second;
     for (auto st : s->sig_stream)
