@@ -171,12 +171,14 @@ typedef struct {
     uint64_t resolve_rounds;  /* in-batch order-resolution iterations so far */
     uint64_t uncertain_docs;  /* documents that needed in-batch resolution */
     uint64_t kernel_launches; /* kernels this library has launched in this process */
-    double sig_ms;            /* device time in the signature stage (CUDA events) */
-    double bloom_ms;          /* device time in the Bloom stage (CUDA events) */
+    double sig_ms;            /* device time in the signature stage (CUDA events; the
+                                 persistent kernel alone in the batched form) */
+    double bloom_ms;          /* device time in the Bloom stage (CUDA events; everything
+                                 else of a chunk in the batched form) */
     uint64_t sig_chunks;      /* signature-stage launches timed in sig_ms */
-    double probe_ms;          /* device time of the stand-alone probe kernel (plain form) */
+    double probe_ms;          /* device time of the Bloom probe kernel (both forms) */
     uint64_t probe_sectors;   /* 32-byte sectors that kernel's probes address (k per band key,
-                                 one per band key in the blocked layout) */
+                                 one per band key in the blocked and exact layouts) */
     double h2d_ms;            /* copy-stream time of the token copies of host inputs (CUDA events) */
     uint64_t h2d_bytes;       /* bytes those copies moved */
     double call_ms;           /* host wall-clock time spent inside dedup calls */
