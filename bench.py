@@ -64,18 +64,19 @@ IMAD_PER_PERMHASH = 4       # two 32x32->64 products (lo and hi halves) per (a*h
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per document of
-# the two roofline kernels, from ncu captures on the 100k-document
-# peS2o-shaped batch (same corpus, same 11 x 116.8 MB filters); a launch's
-# traffic scales with the documents it processes (65,536- and 100,000-document
-# launches agree within 0.5% per document).  Reported only while the kernel's
-# sources, comments aside, hash to the captured state: a changed kernel
-# reports null.
+# the two roofline kernels, from ncu captures (same 11 x 116.8 MB filters as
+# the bench).  Reported only while the kernel's sources, comments aside, hash
+# to the captured state: a changed kernel reports null.
 _CSRC = "paper_2411_04257_gb300/csrc/"
 _TRAFFIC = {
-    "k_batched": {"bytes_per_doc": None,
+    # one launch of 100,000 documents (489.4M tokens): 2,033.8 MB read + 70.3 MB
+    # written; the traffic is the tokens read once, so it scales with the
+    # documents (tokens) a launch processes
+    "k_batched": {"bytes_per_doc": 21040.1,
                   "sources": ["batched_kernels.cuh", "sig_kernels.cuh", "lshb_device.cuh",
-                              "bloom_kernels.cuh", "lshb_internal.h"],
-                  "sha256": None, "profile": None},
+                              "bloom_kernels.cuh", "lshb_internal.h", "segment.h"],
+                  "sha256": "fd8ec505298df244d8fb1334117bb4557697e38a65ebc1fec7c91174a722da33",
+                  "profile": "profiles/k_batched_pes2o100k_ncu.md"},
     "k_probe": {"bytes_per_doc": None,
                 "sources": ["bloom_kernels.cu", "bloom_kernels.cuh", "lshb_device.cuh",
                             "lshb_internal.h"],
@@ -344,6 +345,22 @@ def _serve_bench(local, seconds_per_load=3.0, n_docs=200_000, seed=0):
 
     spec = dataclasses.replace(corpus.serving_requests(seed=seed), n_docs=n_docs)
     off_d, tok_d = sgpu.DeviceCorpus(spec, torch.device("cuda", local)).generate(0, n_docs)
+    torch.cuda.synchronize()
+    # the batched form on the same mix, one call over the whole corpus
+    # resident in HBM: what the server's saturation compares with
+    ixb = LSHBloom(P, BANDS, ROWS, n_expected=100_000_000, fp_rate=1e-5, ngram=NGRAM,
+                   device=local)
+    for _ in range(3):
+        ixb.reset()
+        ixb.dedup(off_d, tok_d)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(5):
+        ixb.reset()
+        ixb.dedup(off_d, tok_d)
+    torch.cuda.synchronize()
+    batched_same_mix = 5 * n_docs / (time.perf_counter() - t0)
+    ixb.close()
     off_h = off_d.cpu().numpy().view(np.uint64)
     tok_h = tok_d.cpu().numpy().view(np.uint32)
     del off_d, tok_d
@@ -386,6 +403,7 @@ def _serve_bench(local, seconds_per_load=3.0, n_docs=200_000, seed=0):
     sat, p50, p99, n = run(burst, [0.0] * len(burst))
     out = {"indexes": 4, "n_expected_per_index": 100_000_000, "max_inflight": 64,
            "mem_budget_gb": 4, "saturation_docs_per_s": sat,
+           "batched_form_same_mix_docs_per_s": batched_same_mix,
            "burst": {"requests": n, "p50_ms": p50, "p99_ms": p99}, "loads": []}
     mean_docs = 4095.0 / np.log(4096.0)
     for frac in (0.25, 0.60, 0.90):
