@@ -539,3 +539,21 @@ def test_dedup_from_keys_matches_oracle(lshb, oracle, layout, lay, insert_all):
     if not insert_all:
         assert st["resolve_rounds"] > 64          # the chain outlasted the sweeps
     ix.close()
+
+
+@pytest.mark.parametrize("exec_mode", ["batched", "plain"])
+def test_dedup_keys_host_buffers_several_chunks(lshb, oracle, corpus, exec_mode):
+    """lshbloom_dedup_keys with host offsets, tokens, flags and keys, over
+    chunks of 300 documents: the batched form keeps the keys band-major on the
+    device and hands them back row-major; keys and flags equal the oracle's."""
+    off, tok = _small_corpus(corpus, n=1000, seed=12)
+    ix = lshb.LSHBloom(121, 11, 11, n_expected=1000, exec_mode=exec_mode, max_batch_docs=300)
+    flags, keys = ix.dedup_keys(off, tok)
+    ref = oracle.OracleIndex(121, 11, 11, n_expected=1000)
+    want_keys = oracle.batch_band_keys(off, tok, 5, ref.a, ref.b, 11, 11)
+    assert isinstance(keys, np.ndarray) and keys.shape == (1000, 11)
+    assert np.array_equal(keys.view(np.uint64), want_keys)
+    assert np.array_equal(np.asarray(flags), ref.dedup_keys(want_keys))
+    for j in (0, 10):
+        assert np.array_equal(ix.filter_bytes(j), ref.filter_bytes(j))
+    ix.close()
