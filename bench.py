@@ -77,10 +77,14 @@ _TRAFFIC = {
                               "bloom_kernels.cuh", "lshb_internal.h", "segment.h"],
                   "sha256": "fd8ec505298df244d8fb1334117bb4557697e38a65ebc1fec7c91174a722da33",
                   "profile": "profiles/k_batched_pes2o100k_ncu.md"},
-    "k_probe": {"bytes_per_doc": None,
+    # measured at the bench's launch size, 333,334 documents per launch (the
+    # probe's L2 reuse grows with the documents of a launch, so a per-document
+    # figure holds for that size): 3,082 MB read + 65 MB written per launch
+    "k_probe": {"bytes_per_doc": 9443.0,
                 "sources": ["bloom_kernels.cu", "bloom_kernels.cuh", "lshb_device.cuh",
                             "lshb_internal.h"],
-                "sha256": None, "profile": None},
+                "sha256": "e26704c4a9cafb933122178638c13f3b1bf3ccd46c226d9b447f82894fd18f03",
+                "profile": "profiles/bloom_kernels_ncu.md"},
 }
 
 
