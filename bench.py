@@ -79,11 +79,11 @@ _TRAFFIC = {
                   "profile": "profiles/k_batched_pes2o100k_ncu.md"},
     # measured at the bench's launch size, 333,334 documents per launch (the
     # probe's L2 reuse grows with the documents of a launch, so a per-document
-    # figure holds for that size): 3,082 MB read + 65 MB written per launch
-    "k_probe": {"bytes_per_doc": 9443.0,
+    # figure holds for that size): 3,094 MB read + 65 MB written per launch
+    "k_probe": {"bytes_per_doc": 9480.0,
                 "sources": ["bloom_kernels.cu", "bloom_kernels.cuh", "lshb_device.cuh",
                             "lshb_internal.h"],
-                "sha256": "e26704c4a9cafb933122178638c13f3b1bf3ccd46c226d9b447f82894fd18f03",
+                "sha256": "5693a153207f23564f535dd04cae3886aee621765f3cc5767d7acba63c342751",
                 "profile": "profiles/bloom_kernels_ncu.md"},
 }
 
