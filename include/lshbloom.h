@@ -173,8 +173,9 @@ typedef struct {
     uint64_t kernel_launches; /* kernels this library has launched in this process */
     double sig_ms;            /* device time in the signature stage (CUDA events; the
                                  persistent kernel alone in the batched form) */
-    double bloom_ms;          /* device time in the Bloom stage (CUDA events; everything
-                                 else of a chunk in the batched form) */
+    double bloom_ms;          /* device time in the Bloom stage (CUDA events; in the
+                                 batched form from the chunk's signatures to its flags,
+                                 overlapping the next chunk's signatures when pipelined) */
     uint64_t sig_chunks;      /* signature-stage launches timed in sig_ms */
     double probe_ms;          /* device time of the Bloom probe kernel (both forms) */
     uint64_t probe_sectors;   /* 32-byte sectors that kernel's probes address (k per band key,
@@ -185,6 +186,8 @@ typedef struct {
     uint64_t host_read_bytes; /* host token bytes the kernels read in place (no copy) */
     uint64_t chunk_docs;      /* batched form: documents per internal chunk now in use
                                  (max_batch_docs, or the autotuner's current choice) */
+    uint64_t pipelined_chunks; /* batched form: chunks whose Bloom stage ran while the next
+                                 chunk's signatures were being computed */
 } lshb_stats;
 
 /* Fill *cfg with defaults: P=121, b=11, r=11, n=5, n_expected=10000,

@@ -10,13 +10,15 @@ multi-pass capture of one launch stays small.
     python -m microbench.bloom_probe --chunk-docs 333334 [--docs 8000000]
         [--layout standard|blocked|exact] [--repeat 1]
 
-Prints one JSON line (documents, launches, duplicates, stage times).
+Prints one JSON line (documents, launches, duplicates, per-call wall times, stage
+times).
 """
 from __future__ import annotations
 
 import argparse
 import dataclasses
 import json
+import time
 
 
 def main(argv=None):
@@ -38,16 +40,20 @@ def main(argv=None):
     torch.cuda.synchronize()
     ix = LSHBloom(121, 11, 11, n_expected=39_000_000, fp_rate=1e-5, ngram=5,
                   max_batch_docs=args.chunk_docs, bloom_layout=args.layout, device=0)
-    dups = []
+    dups, call_ms = [], []
     for _ in range(args.repeat):
         ix.reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         flags = ix.dedup(off, tok)
+        call_ms.append(1e3 * (time.perf_counter() - t0))
         dups.append(int(flags.sum().item()))
     st = ix.stats()
     ix.close()
     print(json.dumps({"docs": args.docs, "tokens": int(off[-1].item()),
                       "chunk_docs": st["chunk_docs"], "layout": args.layout,
-                      "repeat": args.repeat, "dups": dups,
+                      "repeat": args.repeat, "dups": dups, "call_ms": call_ms,
+                      "pipelined_chunks": st["pipelined_chunks"],
                       "launches": st["kernel_launches"], "sig_ms": st["sig_ms"],
                       "bloom_ms": st["bloom_ms"], "probe_ms": st["probe_ms"]}))
 

@@ -40,6 +40,7 @@ class Stats(C.Structure):
         ("probe_ms", C.c_double), ("probe_sectors", C.c_uint64),
         ("h2d_ms", C.c_double), ("h2d_bytes", C.c_uint64), ("call_ms", C.c_double),
         ("host_read_bytes", C.c_uint64), ("chunk_docs", C.c_uint64),
+        ("pipelined_chunks", C.c_uint64),
     ]
 
 

@@ -22,6 +22,8 @@ struct DynParams {
     uint64_t n_items;         // written on the device by the scan
     const Segment *segs;      // nseg > 0: the launch covers these batches instead
     uint32_t nseg;
+    uint32_t active_blocks;   // persistent-kernel blocks that take items (0: all); the
+                              // others return at once and leave their SM slots free
 };
 
 // Where document d of a launch lives: its offsets (indexed by `local`), its
@@ -202,6 +204,8 @@ __global__ void k_expand(const __grid_constant__ BatchArgs A) {
 template <int NG, int PPL>
 __global__ void __launch_bounds__(kBatchThreads) k_batched(const __grid_constant__ BatchArgs A) {
     __shared__ SigSmem<PPL> sm;
+    const DynParams dp = *A.dyn;
+    if (dp.active_blocks && blockIdx.x >= dp.active_blocks) return;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const uint32_t n = NG > 0 ? (uint32_t)NG : A.ngram;
@@ -209,7 +213,6 @@ __global__ void __launch_bounds__(kBatchThreads) k_batched(const __grid_constant
     cf.load(A.c, A.npc, lane);
     uint32_t *hbuf = reinterpret_cast<uint32_t *>(sm.hbuf[wib]);
     uint32_t *sigbuf = sm.sig[wib];
-    const DynParams dp = *A.dyn;
     const uint64_t n_items = min(dp.n_items, A.item_cap);
     for (;;) {
         unsigned long long it = 0;

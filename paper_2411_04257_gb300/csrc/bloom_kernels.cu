@@ -34,8 +34,8 @@ namespace lshb {
 
 // ---- probe and classification ----------------------------------------------------
 
-__global__ void __launch_bounds__(kBloomThreads) k_probe(const __grid_constant__ BloomArgs A) {
-    const uint64_t d = (uint64_t)blockIdx.x * kBloomThreads + threadIdx.x;
+__global__ void __launch_bounds__(kProbeThreads) k_probe(const __grid_constant__ BloomArgs A) {
+    const uint64_t d = (uint64_t)blockIdx.x * kProbeThreads + threadIdx.x;
     const uint32_t j = blockIdx.y;
     if (d >= batch_docs(A)) return;
     uint64_t miss = probe_key<24>(A, j, band_key(A, d, j));
@@ -63,10 +63,10 @@ __global__ void __launch_bounds__(kBloomThreads) k_classify(const __grid_constan
 
 // Status per document and the per-block count of uncertain documents.
 // status: 1 = duplicate whatever the order, 2 = uncertain, 0 = not duplicate.
-__global__ void __launch_bounds__(1024) k_status(const __grid_constant__ BloomArgs A,
-                                                 uint32_t *block_counts) {
-    __shared__ uint32_t warp_cnt[32];
-    const uint64_t d = (uint64_t)blockIdx.x * 1024 + threadIdx.x;
+__global__ void __launch_bounds__(kStatusThreads) k_status(const __grid_constant__ BloomArgs A,
+                                                           uint32_t *block_counts) {
+    __shared__ uint32_t warp_cnt[kStatusThreads / 32];
+    const uint64_t d = (uint64_t)blockIdx.x * kStatusThreads + threadIdx.x;
     uint8_t st = 0;
     if (d < batch_docs(A)) {
         st = A.prehit[d] ? 1 : (A.cand[d] ? 2 : 0);
@@ -77,43 +77,58 @@ __global__ void __launch_bounds__(1024) k_status(const __grid_constant__ BloomAr
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t s = 0;
-        for (int w = 0; w < 32; ++w) s += warp_cnt[w];
+        for (int w = 0; w < kStatusThreads / 32; ++w) s += warp_cnt[w];
         block_counts[blockIdx.x] = s;
     }
 }
 
-// Exclusive scan of the block counts (one block; nb up to a few thousand) and
-// the total in *total.
-__global__ void __launch_bounds__(1024) k_scan_counts(uint32_t *block_counts, uint32_t nb,
-                                                      uint32_t *total) {
-    __shared__ uint32_t part[1024];
+// Exclusive scan of the block counts (one block; nb up to several thousand)
+// and the total in *total.  Each thread takes kScanPer consecutive counts, so
+// a 2^21-document batch (8,192 counts) takes four rounds of the block scan.
+constexpr int kScanPer = 8;
+
+__global__ void __launch_bounds__(kStatusThreads) k_scan_counts(uint32_t *block_counts,
+                                                                uint32_t nb, uint32_t *total) {
+    __shared__ uint32_t part[kStatusThreads];
     __shared__ uint32_t carry;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    for (uint32_t base = 0; base < nb; base += 1024) {
-        const uint32_t i = base + threadIdx.x;
-        const uint32_t v = i < nb ? block_counts[i] : 0u;
-        part[threadIdx.x] = v;
+    for (uint32_t base = 0; base < nb; base += kStatusThreads * kScanPer) {
+        const uint32_t i0 = base + threadIdx.x * kScanPer;
+        uint32_t v[kScanPer];
+        uint32_t sum = 0;
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) {
+            v[k] = i0 + k < nb ? block_counts[i0 + k] : 0u;
+            sum += v[k];
+        }
+        part[threadIdx.x] = sum;
         __syncthreads();
-        for (uint32_t off = 1; off < 1024; off <<= 1) {
+        for (uint32_t off = 1; off < kStatusThreads; off <<= 1) {
             const uint32_t add = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
             __syncthreads();
             part[threadIdx.x] += add;
             __syncthreads();
         }
-        if (i < nb) block_counts[i] = carry + part[threadIdx.x] - v;
+        uint32_t run = carry + part[threadIdx.x] - sum;
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) {
+            if (i0 + k < nb) block_counts[i0 + k] = run;
+            run += v[k];
+        }
         __syncthreads();
-        if (threadIdx.x == 1023) carry += part[1023];
+        if (threadIdx.x == kStatusThreads - 1) carry += part[kStatusThreads - 1];
         __syncthreads();
     }
     if (threadIdx.x == 0) *total = carry;
 }
 
 // Uncertain documents in increasing index order.
-__global__ void __launch_bounds__(1024) k_compact(const __grid_constant__ BloomArgs A,
-                                                  const uint32_t *block_offsets, uint32_t *ulist) {
-    __shared__ uint32_t warp_pre[32];
-    const uint64_t d = (uint64_t)blockIdx.x * 1024 + threadIdx.x;
+__global__ void __launch_bounds__(kStatusThreads) k_compact(const __grid_constant__ BloomArgs A,
+                                                            const uint32_t *block_offsets,
+                                                            uint32_t *ulist) {
+    __shared__ uint32_t warp_pre[kStatusThreads / 32];
+    const uint64_t d = (uint64_t)blockIdx.x * kStatusThreads + threadIdx.x;
     const bool u = d < batch_docs(A) && A.status[d] == 2;
     const uint32_t bal = __ballot_sync(LSHB_FULL_MASK, u);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -121,7 +136,7 @@ __global__ void __launch_bounds__(1024) k_compact(const __grid_constant__ BloomA
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t s = 0;
-        for (int i = 0; i < 32; ++i) {
+        for (int i = 0; i < kStatusThreads / 32; ++i) {
             const uint32_t c = warp_pre[i];
             warp_pre[i] = s;
             s += c;
@@ -431,8 +446,8 @@ static int grid_for(uint64_t n, int threads) {
 }
 
 // (document blocks, bands) grid for n documents.
-static dim3 band_grid(uint64_t n, uint32_t bands) {
-    const uint64_t bx = (n + kBloomThreads - 1) / kBloomThreads;
+static dim3 band_grid(uint64_t n, uint32_t bands, int threads = kBloomThreads) {
+    const uint64_t bx = (n + threads - 1) / threads;
     return dim3((unsigned)(bx ? bx : 1), bands, 1);
 }
 
@@ -474,7 +489,7 @@ static BloomArgs pass_args(BloomArgs a, uint32_t p, uint32_t np) {
 }
 
 cudaError_t launch_probe(const BloomArgs &a, uint64_t dcap, cudaStream_t s) {
-    k_probe<<<band_grid(dcap, a.bands), kBloomThreads, 0, s>>>(pass_args(a, 0, 1));
+    k_probe<<<band_grid(dcap, a.bands, kProbeThreads), kProbeThreads, 0, s>>>(pass_args(a, 0, 1));
     count_launch();
     return cudaGetLastError();
 }
@@ -482,10 +497,10 @@ cudaError_t launch_probe(const BloomArgs &a, uint64_t dcap, cudaStream_t s) {
 cudaError_t launch_classify(const BloomArgs &a, uint64_t dcap, uint32_t *block_counts,
                             uint32_t *total, uint32_t *ulist, cudaStream_t s) {
     k_classify<<<band_grid(dcap, a.bands), kBloomThreads, 0, s>>>(a); count_launch();
-    const uint32_t nb = (uint32_t)((dcap + 1023) / 1024);
-    k_status<<<nb ? nb : 1, 1024, 0, s>>>(a, block_counts); count_launch();
-    k_scan_counts<<<1, 1024, 0, s>>>(block_counts, nb ? nb : 1, total); count_launch();
-    k_compact<<<nb ? nb : 1, 1024, 0, s>>>(a, block_counts, ulist); count_launch();
+    const uint32_t nb = (uint32_t)((dcap + kStatusThreads - 1) / kStatusThreads);
+    k_status<<<nb ? nb : 1, kStatusThreads, 0, s>>>(a, block_counts); count_launch();
+    k_scan_counts<<<1, kStatusThreads, 0, s>>>(block_counts, nb ? nb : 1, total); count_launch();
+    k_compact<<<nb ? nb : 1, kStatusThreads, 0, s>>>(a, block_counts, ulist); count_launch();
     return cudaGetLastError();
 }
 

@@ -15,6 +15,15 @@ constexpr uint32_t kErrQueue = 2u;       // persistent kernel work-queue inconsi
 // p = 1e-5: it stays in the 129 MB L2) and on that band's sketch.
 constexpr int kBloomThreads = 256;
 
+// Block sizes chosen so that every kernel of the stage fits beside the
+// persistent signature kernel in one freed block slot of an SM (10,240
+// registers with that kernel at 9 of its 10 blocks per SM): the batched form
+// runs the Bloom stage of one chunk while the next chunk's signatures are
+// computed.  The probe kernel (60 registers) takes 128-thread blocks, the
+// status/compaction kernels 256 instead of 1024.
+constexpr int kProbeThreads = 128;
+constexpr int kStatusThreads = 256;
+
 struct BloomArgs {
     uint64_t D;
     const uint64_t *D_dev;      // when set, the batch size is read from device memory

@@ -522,7 +522,9 @@ lshb_status lshb::ensure_chunk_scratch(lshbloom *h, uint64_t Dc, uint64_t Tc, bo
     if ((st = h->buf(B_FLAGS).reserve(Dc)) != LSHB_OK) return st;
     if ((st = h->buf(B_INSD).reserve(Dc)) != LSHB_OK) return st;
     if ((st = h->buf(B_ULIST).reserve(Dc * 4)) != LSHB_OK) return st;
-    if ((st = h->buf(B_BLOCKCNT).reserve(((Dc + 1023) / 1024 + 1) * 4)) != LSHB_OK) return st;
+    if ((st = h->buf(B_BLOCKCNT).reserve(((Dc + kStatusThreads - 1) / kStatusThreads + 1) * 4)) !=
+        LSHB_OK)
+        return st;
     if ((st = h->buf(B_OFFSTAGE).reserve((Dc + 1) * 8)) != LSHB_OK) return st;
     if (need_sig || h->passes.size() > 1 || h->cfg.exec_mode == LSHB_EXEC_PLAIN)
         if ((st = h->buf(B_SIG).reserve(Dc * h->P * 4)) != LSHB_OK) return st;
@@ -1075,6 +1077,7 @@ extern "C" lshb_status lshbloom_stats(lshbloom_t *h, lshb_stats *out) {
     out->call_ms = h->t_call_ms;
     out->host_read_bytes = h->host_read_bytes;
     out->chunk_docs = h->max_docs_batched;
+    out->pipelined_chunks = h->pipelined_chunks;
     unsigned long long *cnt = (unsigned long long *)(h->counters + C_POPCOUNT);
     const bool exact = h->layout == LSHB_EXACT_KEYS;
     for (uint32_t j = 0; j < h->bands; ++j) {

@@ -96,6 +96,7 @@ struct lshbloom {
     cudaEvent_t ev_t[3] = {nullptr, nullptr, nullptr};  // stage timers
     double t_sig_ms = 0.0, t_bloom_ms = 0.0;
     uint64_t sig_chunks = 0;
+    uint64_t pipelined_chunks = 0;  // batched form: Bloom stages overlapped with the next signatures
     cudaEvent_t ev_p[2] = {nullptr, nullptr};  // bracket the probe kernel (one-kernel-per-stage form)
     cudaEvent_t ev_order = nullptr;  // orders a synchronous call after the legacy default stream
     double t_probe_ms = 0.0;

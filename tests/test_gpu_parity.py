@@ -252,6 +252,43 @@ def test_dedup_many_calls_and_small_chunks(lshb, oracle, corpus):
                  max_batch_docs=97, max_batch_tokens=5000)
 
 
+@pytest.mark.parametrize("insert_all", [False, True])
+@pytest.mark.parametrize("inputs", ["device", "host_staged"])
+def test_pipelined_chunks_match_oracle(lshb, oracle, corpus, insert_all, inputs):
+    """Short documents over many chunks.  The first call runs its chunks one
+    after the other and measures a Bloom stage that outweighs the signatures,
+    so later calls pipeline them: the next chunk's signatures (in the other
+    of two signature slots) run while this chunk's Bloom stage does.  Flags
+    and every filter byte equal the oracle's over the whole stream."""
+    off, tok = _small_corpus(corpus, n=12000, seed=21, length_median=40, length_min=5,
+                             length_max=400, dup_frac=0.4)
+    want, st = _check_dedup(lshb, oracle, off, tok, calls=[0, 3000, 7000, 12000],
+                            device_inputs=inputs == "device", max_batch_docs=1000,
+                            insert_all=insert_all, stage_host_inputs=inputs == "host_staged")
+    assert want.sum() > 1000
+    assert st["pipelined_chunks"] >= 7, st["pipelined_chunks"]
+
+
+def test_pipelined_chunks_keys_out(lshb, oracle, corpus):
+    """lshbloom_dedup_keys on a pipelined handle: each chunk's keys leave its
+    signature slot row-major; keys and flags equal the oracle's."""
+    off, tok = _small_corpus(corpus, n=6000, seed=22, length_median=40, length_min=5,
+                             length_max=400, dup_frac=0.4)
+    ix = lshb.LSHBloom(121, 11, 11, n_expected=6000, max_batch_docs=500)
+    ref = oracle.OracleIndex(121, 11, 11, n_expected=6000)
+    want_keys = oracle.batch_band_keys(off, tok, 5, ref.a, ref.b, 11, 11)
+    want = ref.dedup_keys(want_keys)
+    first = ix.dedup(*_dev(off[:2001], tok)).cpu().numpy()
+    o2 = off[2000:] - off[2000]
+    flags, keys = ix.dedup_keys(o2, tok[int(off[2000]):])
+    assert ix.stats()["pipelined_chunks"] >= 7
+    assert np.array_equal(keys.view(np.uint64), want_keys[2000:])
+    assert np.array_equal(np.concatenate([first, np.asarray(flags)]), want)
+    for j in (0, 10):
+        assert np.array_equal(ix.filter_bytes(j), ref.filter_bytes(j))
+    ix.close()
+
+
 @pytest.mark.parametrize("stage", [True, False])
 def test_dedup_host_inputs(lshb, oracle, corpus, stage):
     """Pageable host arrays: staged through device buffers (forced), or read in
