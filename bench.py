@@ -69,21 +69,21 @@ IMAD_PER_PERMHASH = 4       # two 32x32->64 products (lo and hi halves) per (a*h
 # to the captured state: a changed kernel reports null.
 _CSRC = "paper_2411_04257_gb300/csrc/"
 _TRAFFIC = {
-    # one launch of 100,000 documents (489.4M tokens): 2,033.8 MB read + 70.3 MB
+    # one launch of 100,000 documents (489.4M tokens): 2,032.8 MB read + 69.8 MB
     # written; the traffic is the tokens read once, so it scales with the
     # documents (tokens) a launch processes
-    "k_batched": {"bytes_per_doc": 21040.1,
+    "k_batched": {"bytes_per_doc": 21026.2,
                   "sources": ["batched_kernels.cuh", "sig_kernels.cuh", "lshb_device.cuh",
                               "bloom_kernels.cuh", "lshb_internal.h", "segment.h"],
-                  "sha256": "fd8ec505298df244d8fb1334117bb4557697e38a65ebc1fec7c91174a722da33",
+                  "sha256": "71ee6a9c8148791df44e1b26758c9865630e0a29b0a90f624769dc36dc83d924",
                   "profile": "profiles/k_batched_pes2o100k_ncu.md"},
     # measured at the bench's launch size, 333,334 documents per launch (the
     # probe's L2 reuse grows with the documents of a launch, so a per-document
-    # figure holds for that size): 3,094 MB read + 65 MB written per launch
-    "k_probe": {"bytes_per_doc": 9480.0,
+    # figure holds for that size): 3,080 MB read + 65 MB written per launch
+    "k_probe": {"bytes_per_doc": 9436.8,
                 "sources": ["bloom_kernels.cu", "bloom_kernels.cuh", "lshb_device.cuh",
                             "lshb_internal.h"],
-                "sha256": "5693a153207f23564f535dd04cae3886aee621765f3cc5767d7acba63c342751",
+                "sha256": "9f4447b299eebe062d0006afd085277cce7a6b0a06dd15fd4488da197d0d261e",
                 "profile": "profiles/bloom_kernels_ncu.md"},
 }
 
