@@ -332,7 +332,7 @@ def run_reference(args):
     return 0
 
 
-def _serve_bench(local, seconds_per_load=3.0, n_docs=200_000, seed=0):
+def _serve_bench(local, seconds_per_load=3.0, n_docs=200_000, seed=0, burst_requests=600):
     """Continuous-batching server over 4 resident indexes (n = 100M each):
     requests of 1-4,096 documents (log-uniform) cut cyclically from a
     serving-shaped corpus (lognormal median 1,000 tokens, 10% near-dups).
@@ -403,7 +403,7 @@ def _serve_bench(local, seconds_per_load=3.0, n_docs=200_000, seed=0):
 
     warm = [next_request() for _ in range(64)]
     run(warm, [0.0] * len(warm))
-    burst = [next_request() for _ in range(600)]
+    burst = [next_request() for _ in range(burst_requests)]
     sat, p50, p99, n = run(burst, [0.0] * len(burst))
     out = {"indexes": 4, "n_expected_per_index": 100_000_000, "max_inflight": 64,
            "mem_budget_gb": 4, "saturation_docs_per_s": sat,
@@ -790,7 +790,7 @@ def run_ours(args):
     del off, tok
     torch.cuda.empty_cache()
     if not args.skip_serve:
-        serve = _serve_bench(local)
+        serve = _serve_bench(local, burst_requests=args.serve_burst)
 
     # the other configurations: parity cases, measured here as sub-records
     configs = None
@@ -892,6 +892,8 @@ def main():
     ap.add_argument("--skip-peaks", action="store_true", help="skip the peak microbenchmarks")
     ap.add_argument("--threaded-docs", type=int, default=100_000,
                     help="documents of the workload the threaded CPU baseline runs")
+    ap.add_argument("--serve-burst", type=int, default=600,
+                    help="requests of the serving burst that measures saturation")
     ap.add_argument("--billion-docs", type=int, default=1_000_000_000)
     ap.add_argument("--billion-chunk", type=int, default=4_000_000)
     args = ap.parse_args()
