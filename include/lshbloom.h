@@ -226,7 +226,10 @@ LSHB_API lshb_status lshbloom_dedup(lshbloom_t *h, const uint64_t *offsets, cons
 /* As lshbloom_dedup with device pointers only, ordered on `stream` (a
  * cudaStream_t; NULL = the legacy default stream).  The host may block while
  * it plans chunks and when a batch needs in-batch order resolution; flags_out
- * is complete when the stream reaches the end of the enqueued work. */
+ * is complete when the stream reaches the end of the enqueued work.  The
+ * batched form may compute the signatures of later chunks on a private
+ * stream of the handle, started after the work enqueued on `stream` before
+ * the call; each chunk's Bloom stage runs on `stream` after them. */
 LSHB_API lshb_status lshbloom_dedup_async(lshbloom_t *h, const uint64_t *offsets, const uint32_t *tokens,
                                  uint64_t D, uint8_t *flags_out, void *stream);
 
