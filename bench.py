@@ -469,8 +469,10 @@ def _timed_mode(ix, off, tok, stream, steps, warmup, sync, local, dev):
              "probe_ms": s1["probe_ms"] - s0["probe_ms"],
              "probe_sectors": s1["probe_sectors"] - s0["probe_sectors"],
              "launches": s1["kernel_launches"] - s0["kernel_launches"],
-             "resolve_rounds": s1["resolve_rounds"] - s0["resolve_rounds"],
-             "uncertain_docs": s1["uncertain_docs"] - s0["uncertain_docs"]}
+             # reset() at the start of every step clears these two counters:
+             # after the last step they hold one step's counts
+             "resolve_rounds_per_step": s1["resolve_rounds"],
+             "uncertain_docs_per_step": s1["uncertain_docs"]}
     return dt, clocks, stage
 
 
@@ -546,8 +548,8 @@ def _config_record(name, factory, n_docs, nexp, local, dev, stream, sync, steps,
              "stage_ms_per_step": {"signature": st["sig_ms"] / steps,
                                    "bloom": st["bloom_ms"] / steps,
                                    "probe": st["probe_ms"] / steps},
-             "resolve_sweeps_per_step": st["resolve_rounds"] / steps,
-             "uncertain_docs_per_step": st["uncertain_docs"] / steps,
+             "resolve_sweeps_per_step": st["resolve_rounds_per_step"],
+             "uncertain_docs_per_step": st["uncertain_docs_per_step"],
              "gpu_launches_per_step": st["launches"] / steps,
              "chunk_docs": ix.stats()["chunk_docs"],
              "dups_per_step": int(flags.sum().item()), "clocks": clocks}
@@ -833,7 +835,8 @@ def run_ours(args):
         "stage_ms_per_step": {m: {"signature": v["sig_ms"] / v["steps"],
                                   "bloom": v["bloom_ms"] / v["steps"],
                                   "probe": v["probe_ms"] / v["steps"],
-                                  "resolve_sweeps": v["resolve_rounds"] / v["steps"]}
+                                  "resolve_sweeps": v["resolve_rounds_per_step"],
+                                  "uncertain_docs": v["uncertain_docs_per_step"]}
                               for m, v in stage.items()},
         "roofline_probe": _probe_roofline(stage.get("batched"), dev_peaks),
         "index_variants": ({lay: {"batched_docs_per_s": results[f"batched/{lay}"]["docs_per_s"],
